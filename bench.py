@@ -1,0 +1,370 @@
+"""Benchmark: MIS-2 + aggregation (+ coarse graph) throughput on GB300.
+
+Default workload (N=1): the 100^3 27-point grid (1,000,000 vertices,
+25,463,592 directed entries, int32 CSR), one full coarsening level per step:
+MIS-2 (Algorithm 1), aggregation (Algorithm 3) and the coarse graph.  The
+metric is edges/s = input entries per step / step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 27pt|small|rmat|batch]
+
+- value: device-resident input, CUDA events around each step, L2 flushed
+  (256 MiB write) before every step, outside the timed interval.
+- e2e: the same metric through the host-buffer C entry point
+  (mis2_coarsen_level_host): host->device copy of the CSR and device->host
+  copy of every output inside the timed interval.
+- roofline: the dominant kernel's algorithmic bytes (the per-round byte model
+  applied to the worklist trace the library reports) over its CUDA-event time.
+- cpu_baseline: the CPU oracle on a bounded sample of the same workload.
+- N > 1 (torchrun): independent replicas, one per GPU (the method does not
+  shard); value = all ranks' edges / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MIS-2+aggregation edges/sec and % HBM roofline on 1 GB300; batched vs plain graphs/sec"
+NOMINAL_HBM_GBS = 8000.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _workload(name):
+    from paper_2204_02934_gb300 import graphgen as gg
+
+    if name == "27pt":
+        return gg.workload_27pt(100), ("27-point 3D grid 100^3 (1,000,000 vertices, 25,463,592 directed entries, "
+                                       "int32 CSR): MIS-2 + aggregation (Alg. 3) + coarse graph, seed 0")
+    if name == "small":
+        return gg.workload_small(), ("5-point 2D grid 100x100 (10,000 vertices, 39,600 directed entries): MIS-2 + "
+                                     "aggregation (Alg. 3) + coarse graph, seed 0")
+    if name == "rmat":
+        g = gg.workload_rmat(22)
+        return g, (f"R-MAT scale 22 (0.57,0.19,0.19,0.05), 8n pairs symmetrised: {g.n} vertices, {g.nnz} entries, "
+                   "int64 rowptr: MIS-2 + aggregation (Alg. 3) + coarse graph, seed 0")
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------ byte model
+def mis2_bytes(trace, n, s):
+    """Algorithmic bytes of the MIS-2 rounds from the per-round worklist
+    trace (W1, W2, D1, D2): row refresh 8*W1; column step (8+s)*W2 + 4*D2 +
+    4*min(n, D2+W2); decide (8+s)*W1 + 4*D1 + 4*min(n, D1+W1); worklist
+    compaction 12*(W1+W2)."""
+    total = 0
+    for w1, w2, d1, d2 in np.asarray(trace, dtype=np.int64).tolist():
+        total += 8 * w1
+        total += (8 + s) * w2 + 4 * d2 + 4 * min(n, d2 + w2)
+        total += (8 + s) * w1 + 4 * d1 + 4 * min(n, d1 + w1)
+        total += 12 * (w1 + w2)
+    return total
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ dist
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(g, budget_s=12.0):
+    """The oracle, as it stands, on the same graph: repeat full levels until
+    about budget_s of CPU time is spent (at least one)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.coarsen_level(g, seed=0)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or el / reps * (reps + 1) > budget_s * 1.5:
+            break
+    return {"value": g.nnz * reps / el, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full coarsening level(s) of the same graph, single-threaded C oracle, "
+                      f"{el:.1f} s on {platform.machine()} ({os.cpu_count()} cores present)"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    g, desc = _workload(args.workload)
+    import oracle
+
+    oracle.build()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.coarsen_level(g, seed=0)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    val = g.nnz * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "edges/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": desc, "n": g.n, "nnz": g.nnz},
+            "cpu_baseline": {"value": val, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} full levels of the workload graph, single-threaded C oracle"},
+            "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2204_02934_gb300 import _build, mis2
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    _build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g, desc = _workload(args.workload)
+    s_bytes = 8 if g.rowptr.dtype == np.int64 else 4
+    loop = mis2.MIS2_LOOP_DEVICE if args.loop == "device" else mis2.MIS2_LOOP_HOST
+    ctx = mis2.Context(g.n, g.nnz, loop=loop, timing=1)
+    dg = mis2.DeviceGraph.from_host(g, dev)
+    n = g.n
+    in_set = torch.empty(n, dtype=torch.uint8, device=dev)
+    roots = torch.empty(n, dtype=torch.int32, device=dev)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    c_rowptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    c_colind = torch.empty(g.nnz, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return mis2.mis2_coarsen_level(ctx.handle, dg.csr, 0, in_set, roots, labels, c_rowptr, c_colind, g.nnz,
+                                       stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms_total = 0.0
+    kernel_ms = np.zeros(mis2.MIS2_NUM_KERNEL_CLASSES)
+    kernel_launch = np.zeros(mis2.MIS2_NUM_KERNEL_CLASSES, dtype=np.int64)
+    launches = 0
+    loop_bytes = 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev0.record(stream)
+        nr, na, cn = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms_total += ev0.elapsed_time(ev1)
+        st = ctx.stats()
+        kernel_ms += np.array(st.kernel_ms[:])
+        kernel_launch += np.array(st.kernel_launches[:], dtype=np.int64)
+        launches += st.launches
+        tr = np.array(st.trace, dtype=np.int64)[:min(st.rounds, mis2.MIS2_TRACE_CAP)]
+        tr2 = np.array(st.trace2, dtype=np.int64)[:min(st.rounds2, mis2.MIS2_TRACE_CAP)]
+        loop_bytes += mis2_bytes(tr, n, s_bytes) + mis2_bytes(tr2, n, s_bytes)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_local = ms_total / 1e3
+    t_max = t_local
+    if ws > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * g.nnz * args.steps / t_max
+
+    # ---- end to end through the host-buffer entry point
+    rp_h = torch.from_numpy(np.ascontiguousarray(g.rowptr)).pin_memory()
+    ci_h = torch.from_numpy(np.ascontiguousarray(g.colind)).pin_memory()
+    o_in = torch.empty(n, dtype=torch.uint8).pin_memory()
+    o_roots = torch.empty(n, dtype=torch.int32).pin_memory()
+    o_labels = torch.empty(n, dtype=torch.int32).pin_memory()
+    o_crp = torch.empty(n + 1, dtype=torch.int32).pin_memory()
+    o_cci = torch.empty(g.nnz, dtype=torch.int32).pin_memory()
+    hcsr = mis2.mis2_csr(n, g.nnz, 1 if s_bytes == 8 else 0, 0, rp_h.data_ptr(), ci_h.data_ptr())
+    e2e_times, d2h = [], 0
+
+    def e2e_step():
+        return mis2.mis2_coarsen_level_host(ctx.handle, hcsr, 0, o_in, o_roots, o_labels, o_crp, o_cci, g.nnz,
+                                            stream)
+
+    for _ in range(2):
+        e2e_step()
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nr, na, cn = e2e_step()
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = n + 4 * nr + 4 * n + 4 * (na + 1) + 4 * cn
+    h2d = rp_h.numel() * rp_h.element_size() + ci_h.numel() * 4
+    e2e_val = ws * g.nnz * len(e2e_times) / sum(e2e_times)
+
+    if rank != 0:
+        if ws > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+    # ---- roofline of the dominant kernel class
+    peak, peak_kind = _peaks()
+    names = mis2.KERNEL_CLASSES
+    dom = int(np.argmax(kernel_ms))
+    dom_ms = kernel_ms[dom]
+    roofline = None
+    if names[dom] == "device_loop" and dom_ms > 0:
+        achieved = loop_bytes / (dom_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_mis_loop (MIS-2 rounds, device loop)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
+                    "traffic": _traffic_from_profile("k_mis_loop"),
+                    "bytes_per_step": loop_bytes / args.steps,
+                    "kernel_ms_per_step": dom_ms / args.steps,
+                    "launches_per_step": int(kernel_launch[dom] // args.steps)}
+    breakdown = {names[k]: round(kernel_ms[k] / args.steps, 4) for k in range(len(names)) if kernel_ms[k] > 0}
+    line = {"metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": desc, "n": g.n, "nnz": g.nnz, "loop": args.loop,
+                       "l2": "flushed (256 MiB write) before every timed step", "parallelism":
+                       "replicas only" if ws > 1 else "single GPU"},
+            "e2e": {"value": e2e_val, "unit": "edges/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "kernel_ms_per_step": breakdown,
+            "clocks": ck,
+            "mis2": {"n_roots": int(nr), "n_aggs": int(na), "c_nnz": int(cn)}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(g, args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _traffic_from_profile(kernel):
+    """dram bytes per launch recorded by an ncu capture of this kernel, when
+    the recorded source digest still matches the library sources."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for ln in open(p):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    try:
+        from paper_2204_02934_gb300 import _build
+
+        if vals.get("source_digest") != _build.source_digest():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat"])
+    ap.add_argument("--loop", default="device", choices=["device", "host"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,222 @@
+/*
+ * mis2.h -- C ABI of the GB300 (sm_103a) MIS-2 / aggregation / coarsening
+ * library.
+ *
+ * The three calls follow the problem statement of Kelley & Rajamanickam,
+ * "Parallel, Portable Algorithms for Distance-2 Maximal Independent Set and
+ * Graph Coarsening" (arXiv 2204.02934):
+ *
+ *   mis2_run        Algorithm 1 (Section III-A): a distance-2 maximal
+ *                   independent set of an undirected graph G = (V, E)
+ *                   (Section I).  Returns the in-set flags and root list.
+ *   mis2_aggregate  Algorithm 3 (Section III-B), or Algorithm 2 in BASIC
+ *                   mode: one aggregate id per vertex.
+ *   mis2_coarsen    the coarsened graph A_c with the vertex -> cluster map
+ *                   (Section III-C, the setup of Algorithm 4).
+ *
+ * Conventions shared by every call
+ *   - Graph input is CSR: rowptr (int32 or int64, n+1 entries) and colind
+ *     (int32, nnz entries), both in DEVICE memory owned by the caller.  The
+ *     graph must be symmetric (undirected, Section I); this is not checked
+ *     unless debug_checks is set.  Self-loops are allowed everywhere.
+ *     Duplicate entries are allowed in mis2_run (they change no minimum,
+ *     "any" or "all" of Algorithm 1), but aggregation counts neighbours over
+ *     the edge set (the ">= 2" test of phase 2, the coupling of phase 3), so
+ *     rows passed to mis2_aggregate / mis2_coarsen_level must list each
+ *     neighbour once.
+ *   - Every output pointer is DEVICE memory owned by the caller unless
+ *     marked "host".  The library owns only the scratch memory inside its
+ *     context, sized at creation.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     return a count through a host pointer synchronise that stream before
+ *     returning; no other host synchronisation is performed.
+ *   - Results are bit-identical run to run and independent of launch
+ *     configuration (every phase is a per-vertex map over arrays written in
+ *     earlier phases; counts use integer atomics).
+ *   - A context is not thread-safe: use one context per host thread/stream.
+ *   - Return value: MIS2_OK (0) or a negative mis2_status.  After
+ *     MIS2_ERR_CUDA the CUDA error string is available through
+ *     mis2_last_error().
+ */
+#ifndef MIS2_GB300_H
+#define MIS2_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MIS2_OK = 0,
+  MIS2_ERR_INVALID_ARG = -1,   /* NULL pointer, negative size, n >= 2^32 - 2, size above capacity */
+  MIS2_ERR_OUT_OF_MEMORY = -2, /* context scratch too small, or cudaMalloc failed */
+  MIS2_ERR_CUDA = -3,          /* a CUDA runtime call failed; see mis2_last_error() */
+  MIS2_ERR_BAD_GRAPH = -4,     /* debug_checks: malformed CSR, or roots not an MIS-2 */
+  MIS2_ERR_TIMEOUT = -5,       /* a device-side barrier gave up after spin_limit polls */
+  MIS2_ERR_NO_PROGRESS = -6    /* round cap (n + 1 rounds) reached */
+} mis2_status;
+
+/* Aggregation modes. */
+enum { MIS2_AGG_ALG3 = 0, MIS2_AGG_BASIC = 1 };
+
+/* Priority hash variants (Section V-A, Table I).  XORSHIFT_STAR is the
+ * paper's choice and the default; the others exist for the ablation. */
+enum { MIS2_HASH_XORSHIFT_STAR = 0, MIS2_HASH_XORSHIFT = 1, MIS2_HASH_FIXED = 2 };
+
+/* Round-loop drivers: HOST reads the worklist size back after every round
+ * (one stream synchronisation per round); DEVICE runs the whole round loop
+ * inside one persistent cooperative kernel with grid-wide barriers. */
+enum { MIS2_LOOP_HOST = 0, MIS2_LOOP_DEVICE = 1 };
+
+typedef struct {
+  int64_t n;            /* number of vertices, 0 <= n < 2^31 */
+  int64_t nnz;          /* number of colind entries, 0 <= nnz < 2^31 */
+  int32_t rowptr_is_64; /* 0: rowptr is int32_t[n+1]; 1: int64_t[n+1] */
+  int32_t reserved;
+  const void* rowptr;   /* device */
+  const int32_t* colind;/* device, 4-byte aligned (16-byte alignment enables vector loads) */
+} mis2_csr;
+
+typedef struct {
+  int32_t hash_variant;   /* MIS2_HASH_*; default XORSHIFT_STAR */
+  int32_t agg_mode;       /* MIS2_AGG_*; default ALG3 */
+  int32_t group_lanes;    /* lanes per low-degree row: 0 = pick from average degree, else 1,2,4,8,16,32 */
+  int32_t warp_degree;    /* rows with degree >= this get a full warp (default 64) */
+  int32_t block_degree;   /* rows with degree >= this get a full block (default 2048) */
+  int32_t block_size;     /* threads per block for row kernels (default 256) */
+  int32_t loop;           /* MIS2_LOOP_*; default DEVICE */
+  int32_t debug_checks;   /* validate CSR and roots (extra passes); default 0 */
+  int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
+  int32_t reserved;
+  int64_t spin_limit;     /* polls before a device barrier reports MIS2_ERR_TIMEOUT */
+} mis2_config;
+
+/* Per-call statistics of the last mis2_run / mis2_aggregate / mis2_coarsen /
+ * mis2_coarsen_level on a context.  trace[r] = {W1, W2, D1, D2}: worklist
+ * sizes and summed row lengths at the start of MIS-2 round r (phase-1 MIS-2
+ * in trace, phase-2 MIS-2 in trace2), up to MIS2_TRACE_CAP rounds. */
+#define MIS2_TRACE_CAP 64
+#define MIS2_NUM_KERNEL_CLASSES 8
+typedef struct {
+  int32_t rounds;           /* rounds of the phase-1 MIS-2 (Algorithm 1 loop count) */
+  int32_t rounds2;          /* rounds of the phase-2 MIS-2 (0 in BASIC mode) */
+  int64_t n_roots;          /* |MIS-2| */
+  int64_t n_phase1;         /* phase-1 aggregates */
+  int64_t n_aggs;           /* all aggregates */
+  int64_t c_nnz;            /* coarse graph entries */
+  int64_t trace[MIS2_TRACE_CAP][4];
+  int64_t trace2[MIS2_TRACE_CAP][4];
+  /* timing (config.timing != 0): total ms and launches per kernel class:
+   * 0 init, 1 column, 2 decide, 3 roots/compaction, 4 aggregation,
+   * 5 coarse graph, 6 device-loop MIS-2 kernel, 7 other */
+  double kernel_ms[MIS2_NUM_KERNEL_CLASSES];
+  int64_t kernel_launches[MIS2_NUM_KERNEL_CLASSES];
+  int64_t launches;         /* CUDA kernels launched by the last call (always counted) */
+} mis2_stats;
+
+typedef struct mis2_ctx mis2_ctx;
+
+/* Fill *cfg with the defaults listed above. */
+void mis2_config_default(mis2_config* cfg);
+
+/* Create a context whose scratch holds graphs of up to max_n vertices and
+ * max_nnz entries (allocated now with cudaMalloc on the current device).
+ * cfg may be NULL (defaults).  *ctx receives the handle; on failure *ctx is
+ * NULL and nothing stays allocated. */
+int mis2_ctx_create(mis2_ctx** ctx, int64_t max_n, int64_t max_nnz, const mis2_config* cfg);
+
+/* Free a context and its scratch; NULL is ignored.  Synchronises the device. */
+int mis2_ctx_destroy(mis2_ctx* ctx);
+
+/* Replace the context's configuration (same validation as create). */
+int mis2_ctx_set_config(mis2_ctx* ctx, const mis2_config* cfg);
+
+/* Copy the statistics of the last call into *out (host). */
+int mis2_get_stats(const mis2_ctx* ctx, mis2_stats* out);
+
+/*
+ * MIS-2 of `g` (Algorithm 1 with the hashed priority of Section V-A and the
+ * packed tuples of Section V-C, Eq. 1).
+ *   seed      xored into the hash; 0 gives the paper's h(iter, v).
+ *   in_set    uint8[n], device: 1 for vertices in the MIS-2, else 0.  May be NULL.
+ *   roots     int32[n] capacity, device: MIS-2 vertices ascending.  May be NULL.
+ *   n_roots   host: |MIS-2|.  n_rounds: host, may be NULL.
+ * Synchronises `stream`.
+ */
+int mis2_run(mis2_ctx* ctx, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int32_t* roots,
+             int64_t* n_roots, int32_t* n_rounds, void* stream);
+
+/*
+ * Test hook for the worked example of Fig. 1: like mis2_run, but round r
+ * uses priority prio_table[r*n + v] (host, uint32, table_rounds * n
+ * entries) instead of the hash for r < table_rounds.  Priorities must be
+ * below 2^(32-b), b = ceil(log2(n+2)).
+ */
+int mis2_run_with_priorities(mis2_ctx* ctx, const mis2_csr* g, const uint32_t* prio_table,
+                             int32_t table_rounds, uint8_t* in_set, int32_t* roots,
+                             int64_t* n_roots, int32_t* n_rounds, void* stream);
+
+/*
+ * Aggregation (Algorithm 3, or Algorithm 2 when mode = MIS2_AGG_BASIC).
+ *   roots     int32[n_roots], device, ascending: an MIS-2 of g (e.g. from mis2_run).
+ *   labels    int32[n], device: aggregate id of each vertex, in [0, *n_aggs).
+ *             Phase-1 aggregates are numbered by ascending root, then
+ *             phase-2 aggregates by ascending root.
+ *   n_aggs    host.
+ * The phase-2 MIS-2 uses the same seed and restarts its round counter at 0.
+ * Synchronises `stream`.
+ */
+int mis2_aggregate(mis2_ctx* ctx, const mis2_csr* g, const int32_t* roots, int64_t n_roots,
+                   uint64_t seed, int32_t mode, int32_t* labels, int64_t* n_aggs, void* stream);
+
+/*
+ * Coarse graph of an aggregation: row A lists, ascending and once each,
+ * every aggregate B != A holding a fine neighbour of a member of A.
+ *   labels      int32[n], device, values in [0, n_aggs).
+ *   c_rowptr    int32[n_aggs + 1], device.
+ *   c_colind    int32[c_colind_cap], device; c_colind_cap >= nnz always suffices.
+ *   c_nnz       host.
+ * Synchronises `stream`.
+ */
+int mis2_coarsen(mis2_ctx* ctx, const mis2_csr* g, const int32_t* labels, int64_t n_aggs,
+                 int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz,
+                 void* stream);
+
+/*
+ * One full coarsening level: mis2_run, then mis2_aggregate in the
+ * context's agg_mode, then mis2_coarsen.  Device outputs as above
+ * (in_set and roots may be NULL).  Host outputs n_roots, n_aggs, c_nnz may
+ * be NULL.  Synchronises `stream`.
+ */
+int mis2_coarsen_level(mis2_ctx* ctx, const mis2_csr* g, uint64_t seed, uint8_t* in_set,
+                       int32_t* roots, int32_t* labels, int32_t* c_rowptr, int32_t* c_colind,
+                       int64_t c_colind_cap, int64_t* n_roots, int64_t* n_aggs, int64_t* c_nnz,
+                       void* stream);
+
+/*
+ * Same as mis2_coarsen_level, with every buffer in HOST memory (pinned
+ * memory gives asynchronous copies): the graph is copied into context
+ * scratch, processed, and the outputs copied back.  rowptr is int32 or
+ * int64 as g->rowptr_is_64 says; g->rowptr and g->colind are host pointers
+ * here.  The context needs max_nnz >= nnz for the copy of colind.
+ */
+int mis2_coarsen_level_host(mis2_ctx* ctx, const mis2_csr* g_host, uint64_t seed,
+                            uint8_t* in_set, int32_t* roots, int32_t* labels, int32_t* c_rowptr,
+                            int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
+                            int64_t* n_aggs, int64_t* c_nnz, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+const char* mis2_status_string(int status);
+
+/* Text of the last CUDA error seen by the library in this thread ("" if none). */
+const char* mis2_last_error(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* mis2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIS2_GB300_H */

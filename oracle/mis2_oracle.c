@@ -252,8 +252,8 @@ int oracle_aggregate(int64_t n, const int64_t* rowptr, const int32_t* colind,
     labels[v] = (int32_t)k;
     for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++) {
       int64_t u = colind[e];
-      if (u == v) continue;
-      if (labels[u] != -1) return ORC_ERR_NOT_MIS2; /* roots closer than 3 */
+      if (u == v || labels[u] == (int32_t)k) continue; /* self-loop or duplicate entry */
+      if (labels[u] != -1) return ORC_ERR_NOT_MIS2;       /* roots closer than 3 */
       labels[u] = (int32_t)k;
     }
     k++;

@@ -1,0 +1,209 @@
+// device_loop.cu -- the whole round loop of Algorithm 1 in one persistent
+// cooperative kernel: every block stays resident, phases are separated by a
+// grid-wide barrier, and the loop ends when worklist1 is empty (read by all
+// blocks right after the decide barrier).  No host synchronisation per
+// round.  Every barrier wait is bounded: after spin_limit polls a block
+// raises the timeout flag, all blocks leave, and the host reports
+// MIS2_ERR_TIMEOUT instead of hanging.
+#include <algorithm>
+
+#include "internal.h"
+#include "mis_rows.cuh"
+
+namespace mis2 {
+
+constexpr int kErrTimeout = 1;
+constexpr int kErrNoProgress = 4;
+
+__device__ __forceinline__ int ld_acquire_i32(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_i32(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *reinterpret_cast<const volatile int32_t*>(p); }
+
+// Sense-free generation barrier over all blocks of the grid.  Returns false
+// (in every thread of the block) when this block gave up waiting or another
+// block already reported a timeout.
+__device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t* gen, int32_t* err, int64_t spin_limit) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int my_gen = ld_acquire_i32(gen);
+    __threadfence();
+    const int arrived = atomicAdd(count, 1);
+    ok = 1;
+    if (arrived == (int)gridDim.x - 1) {
+      atomicExch(count, 0);
+      __threadfence();
+      st_release_i32(gen, my_gen + 1);
+    } else {
+      int64_t spins = 0;
+      while (ld_acquire_i32(gen) == my_gen) {
+        if (++spins > spin_limit || (ld_volatile_i32(err) & kErrTimeout)) {
+          atomicOr(err, kErrTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct LoopArgs {
+  RowLists wl1[2];
+  RowLists wl2[2];
+  uint32_t* T;
+  uint32_t* M;
+  int32_t* ctr;
+  int64_t* dtr;  // trace of this MIS-2 (MIS2_TRACE_CAP x 4)
+  const int32_t* labels;
+  int64_t spin_limit;
+  int32_t warp_degree;
+  int32_t block_degree;
+  int32_t max_rounds;
+  int32_t pad;
+};
+
+template <int G, typename I>
+__global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
+  __shared__ uint32_t sh[40];
+  int32_t* ctr = a.ctr;
+  int32_t* bar_count = ctr + kCtrBarrier;
+  int32_t* bar_gen = ctr + kCtrBarrier + 1;
+  int32_t* err = ctr + kCtrErr;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+
+  mis_init_rows<I>(g, a.labels, p, a.T, a.M, a.wl1[0], a.wl2[0], ctr + ctr_c1(0, 0), ctr + ctr_c2(0, 0),
+                   a.warp_degree, a.block_degree, tid, nthreads);
+  if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit)) return;
+
+  int r = 0;
+  for (;; r++) {
+    const int slot = r % 3, nslot = (r + 1) % 3, zslot = (r + 2) % 3;
+    int n1[kClasses], n2[kClasses];
+    int w1 = 0, w2 = 0;
+#pragma unroll
+    for (int k = 0; k < kClasses; k++) {
+      n1[k] = ld_volatile_i32(ctr + ctr_c1(slot, k));
+      n2[k] = ld_volatile_i32(ctr + ctr_c2(slot, k));
+      w1 += n1[k];
+      w2 += n2[k];
+    }
+    if (w1 == 0) break;
+    if (r > a.max_rounds) {
+      if (tid == 0) atomicOr(err, kErrNoProgress);
+      break;
+    }
+    const bool tr_on = a.dtr != nullptr && r < MIS2_TRACE_CAP;
+    int64_t* d2 = tr_on ? a.dtr + r * 4 + 3 : nullptr;
+    int64_t* d1 = tr_on ? a.dtr + r * 4 + 2 : nullptr;
+    const RowLists in2 = a.wl2[r & 1], out2 = a.wl2[(r + 1) & 1];
+    const RowLists in1 = a.wl1[r & 1], out1 = a.wl1[(r + 1) & 1];
+    // ---- column step
+    if (tid < kClasses) ctr[ctr_c1(nslot, (int)tid)] = 0;
+    if (tid == 0 && tr_on) a.dtr[r * 4 + 1] = w2;
+    column_group_rows<G, I, false>(g, a.T, a.M, in2.l[0], n2[0], out2.l[0], ctr + ctr_c2(nslot, 0), d2, warp,
+                                   nwarps);
+    if (n2[1] > 0)
+      column_group_rows<32, I, false>(g, a.T, a.M, in2.l[1], n2[1], out2.l[1], ctr + ctr_c2(nslot, 1), d2, warp,
+                                      nwarps);
+    if (n2[2] > 0)
+      column_block_rows<I, false>(g, a.T, a.M, in2.l[2], n2[2], out2.l[2], ctr + ctr_c2(nslot, 2), d2, blockIdx.x,
+                                  gridDim.x, sh);
+    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit)) return;
+    // ---- decide step (with the next round's row refresh)
+    if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
+    if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = w1;
+    decide_group_rows<G, I, false>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
+                                   (uint32_t)(r + 1), warp, nwarps);
+    if (n1[1] > 0)
+      decide_group_rows<32, I, false>(g, a.T, a.M, in1.l[1], n1[1], out1.l[1], ctr + ctr_c1(nslot, 1), d1, p,
+                                      (uint32_t)(r + 1), warp, nwarps);
+    if (n1[2] > 0)
+      decide_block_rows<I, false>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
+                                  (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
+    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit)) return;
+  }
+  if (tid == 0) ctr[kCtrRounds] = r;
+}
+
+template <int G, typename I>
+static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cudaStream_t st) {
+  auto kern = k_mis_loop<G, I>;
+  int per_sm = 0;
+  MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+  if (per_sm < 1) return MIS2_ERR_CUDA;
+  const int blocks = c->sm_count * std::min(per_sm, 4);
+  c->device_loop_blocks = blocks;
+  void* args[] = {&gv, &p, &la};
+  MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+  c->launches++;
+  return MIS2_OK;
+}
+
+template <typename I>
+static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
+                           int trace_phase, cudaStream_t st, int32_t* rounds) {
+  Scratch& s = c->s;
+  GraphView<I> gv;
+  gv.rowptr = static_cast<const I*>(g.rowptr);
+  gv.colind = g.colind;
+  gv.n = g.n;
+  gv.nnz = g.nnz;
+  gv.vec = g.vec ? 1 : 0;
+  gv.pad = 0;
+  LoopArgs la;
+  for (int b = 0; b < 2; b++)
+    for (int k = 0; k < kClasses; k++) {
+      la.wl1[b].l[k] = s.wl1[b][k];
+      la.wl2[b].l[k] = s.wl2[b][k];
+    }
+  la.T = s.T;
+  la.M = s.M;
+  la.ctr = s.ctr;
+  la.dtr = s.dtrace + (int64_t)trace_phase * MIS2_TRACE_CAP * 4;
+  la.labels = labels;
+  la.spin_limit = c->cfg.spin_limit;
+  la.warp_degree = c->cfg.warp_degree;
+  la.block_degree = c->cfg.block_degree;
+  la.max_rounds = (int32_t)std::min<int64_t>(g.n, (int64_t)1 << 30);
+  la.pad = 0;
+  MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(la.dtr, 0, MIS2_TRACE_CAP * 4 * sizeof(int64_t), st));
+  timer_begin(c, kKcDeviceLoop, st);
+  int rc;
+  switch (pick_group_lanes(c, g)) {
+    case 1: rc = launch_loop<1, I>(c, gv, p, la, st); break;
+    case 2: rc = launch_loop<2, I>(c, gv, p, la, st); break;
+    case 4: rc = launch_loop<4, I>(c, gv, p, la, st); break;
+    case 8: rc = launch_loop<8, I>(c, gv, p, la, st); break;
+    case 16: rc = launch_loop<16, I>(c, gv, p, la, st); break;
+    default: rc = launch_loop<32, I>(c, gv, p, la, st); break;
+  }
+  timer_end(c, st);
+  if (rc != MIS2_OK) return rc;
+  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MIS2_CUDA(cudaStreamSynchronize(st));
+  if (c->h_ctr[kCtrErr] & kErrTimeout) return MIS2_ERR_TIMEOUT;
+  if (c->h_ctr[kCtrErr] & kErrNoProgress) return MIS2_ERR_NO_PROGRESS;
+  *rounds = c->h_ctr[kCtrRounds];
+  return MIS2_OK;
+}
+
+int mis2_rounds_device(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p, int trace_phase,
+                       cudaStream_t st, int32_t* rounds) {
+  return g.rp64 ? rounds_device_t<int64_t>(c, g, labels, p, trace_phase, st, rounds)
+                : rounds_device_t<int32_t>(c, g, labels, p, trace_phase, st, rounds);
+}
+
+}  // namespace mis2

@@ -1,0 +1,173 @@
+// internal.h -- host-side context and the launchers shared by the
+// translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace mis2 {
+
+// ------------------------------------------------------------- counter words
+// Worklist sizes rotate over three slots per round r: input slot r%3, output
+// slot (r+1)%3, and slot (r+2)%3 is cleared during round r for round r+1.
+__host__ __device__ inline int ctr_c1(int slot, int cls) { return slot * kClasses + cls; }
+__host__ __device__ inline int ctr_c2(int slot, int cls) { return 9 + slot * kClasses + cls; }
+enum : int {
+  kCtrRoots = 18,    // |MIS-2| from the root compaction
+  kCtrM2 = 19,       // phase-2 MIS-2 size
+  kCtrQual = 20,     // qualifying phase-2 roots
+  kCtrHeavy = 21,    // deferred heavy rows
+  kCtrLeft = 22,     // phase-3 leftovers (group rows)
+  kCtrLeftHeavy = 23,
+  kCtrLarge = 24,    // coarse rows needing the block path
+  kCtrCnnz = 25,     // coarse nnz
+  kCtrErr = 26,      // device error flags (bit 0: barrier timeout)
+  kCtrRounds = 27,   // rounds of the device loop
+  kCtrBarrier = 28,  // grid barrier: arrive count (28), generation (29)
+  kCtrWords = 64
+};
+constexpr int kReadbackWords = 32;
+
+enum KernelClass : int {
+  kKcInit = 0,
+  kKcColumn = 1,
+  kKcDecide = 2,
+  kKcCompact = 3,
+  kKcAggregate = 4,
+  kKcCoarse = 5,
+  kKcDeviceLoop = 6,
+  kKcOther = 7
+};
+
+struct Scratch {
+  uint32_t* T = nullptr;
+  uint32_t* M = nullptr;
+  int32_t* wl1[2][kClasses] = {};
+  int32_t* wl2[2][kClasses] = {};
+  int32_t* ctr = nullptr;
+  int64_t* dtrace = nullptr;  // [2][MIS2_TRACE_CAP][4]
+  int32_t* tile = nullptr;
+  int32_t* roots2 = nullptr;
+  int32_t* qlist = nullptr;
+  uint8_t* qflag = nullptr;
+  int32_t* tent = nullptr;
+  int32_t* aggsize = nullptr;
+  int32_t* left = nullptr;
+  int32_t* left_heavy = nullptr;
+  int32_t* roots_tmp = nullptr;  // root list when the caller passes none
+  int32_t* agg_cnt = nullptr;
+  int32_t* agg_ptr = nullptr;
+  int32_t* ub = nullptr;
+  int32_t* ub_ptr = nullptr;
+  int32_t* cursor = nullptr;
+  int32_t* members = nullptr;
+  int32_t* c_cnt = nullptr;
+  int32_t* lo = nullptr;
+  int32_t* hi = nullptr;
+  int32_t* large = nullptr;
+  int32_t* tmp = nullptr;        // coarse rows before packing (max_nnz)
+  int32_t* labels_tmp = nullptr; // labels when the caller passes none
+};
+
+struct HostStage {  // device copies for the host-buffer entry point
+  void* rowptr = nullptr;
+  int32_t* colind = nullptr;
+  uint8_t* in_set = nullptr;
+  int32_t* roots = nullptr;
+  int32_t* labels = nullptr;
+  int32_t* c_rowptr = nullptr;
+  int32_t* c_colind = nullptr;
+  int64_t cap_n = 0, cap_nnz = 0;
+};
+
+struct Timer {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cls;
+  size_t used = 0;
+};
+
+}  // namespace mis2
+
+struct mis2_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int64_t max_n = 0, max_nnz = 0;
+  mis2_config cfg{};
+  mis2_stats stats{};
+  mis2::Scratch s;
+  mis2::HostStage stage;
+  int32_t* h_ctr = nullptr;  // pinned readback of counter words
+  int64_t* h_trace = nullptr;  // pinned readback of the traces
+  mis2::Timer timer;
+  std::vector<void*> allocations;
+  int device_loop_blocks = 0;  // co-resident blocks of the device-loop kernel
+  int64_t launches = 0;        // kernels launched by the current call
+};
+
+namespace mis2 {
+
+// Graph as the launchers see it.
+struct GraphArgs {
+  int64_t n, nnz;
+  bool rp64;
+  const void* rowptr;
+  const int32_t* colind;
+  bool vec;
+};
+
+int set_cuda_error(cudaError_t e);
+#define MIS2_CUDA(call)                                     \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return ::mis2::set_cuda_error(_e); \
+  } while (0)
+#define MIS2_TRY(call)               \
+  do {                               \
+    int _rc = (call);                \
+    if (_rc != MIS2_OK) return _rc;  \
+  } while (0)
+
+// timing helpers: bracket a launch with events when cfg.timing is set
+void timer_begin(mis2_ctx* c, int cls, cudaStream_t st);
+void timer_end(mis2_ctx* c, cudaStream_t st);
+void timer_reset(mis2_ctx* c);
+int timer_collect(mis2_ctx* c);
+
+int pick_group_lanes(const mis2_ctx* c, const GraphArgs& g);
+int grid_for(const mis2_ctx* c, int64_t items, int items_per_block, int blocks_per_sm = 8);
+
+// MIS-2 of g (labels == null) or of {v : labels[v] == -1}; leaves T with
+// IN/OUT.  trace_phase 0/1 selects the trace slot.  Host-driven loop.
+int mis2_rounds_host(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
+                     int trace_phase, cudaStream_t st, int32_t* rounds);
+// Same through the persistent device-loop kernel.
+int mis2_rounds_device(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
+                       int trace_phase, cudaStream_t st, int32_t* rounds);
+// Ordered compaction of {v : T_v = IN}: ascending roots, flags, count on
+// device at ctr[kCtrRoots + which] (which: 0 roots, 1 phase-2 roots).
+int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32_t* count_dev,
+                   cudaStream_t st);
+// Exclusive scan of vals[0, n) into out[0, n], out[n] = total; total also
+// stored at *total_dev when not null.
+int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out, int32_t* total_dev,
+                       cudaStream_t st);
+// Ordered compaction of indices j < n with flags[j] != 0 mapped through
+// map[j] (map null: j itself) into out; count to *count_dev.
+int compact_flags(mis2_ctx* c, const uint8_t* flags, const int32_t* map, int64_t n, int32_t* out,
+                  int32_t* count_dev, cudaStream_t st);
+
+int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,
+                   int mode, int32_t* labels, int64_t* n_aggs, cudaStream_t st);
+int coarsen_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
+                 int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st);
+int run_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, uint8_t* in_set, int32_t* roots,
+             int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
+
+PrioCfg make_prio(const mis2_ctx* c, int64_t n, uint64_t seed);
+
+}  // namespace mis2

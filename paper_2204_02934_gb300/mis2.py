@@ -1,0 +1,340 @@
+"""Python binding of the C ABI in include/mis2.h (argument marshalling only).
+
+Every function named mis2_* here calls the C function of the same name in
+libmis2_gb300.so through ctypes; all computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is missing or fails to
+load, importing the binding raises.
+
+Device buffers come from torch (CUDA tensors); streams are torch streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+MIS2_OK = 0
+STATUS = {
+    0: "MIS2_OK", -1: "MIS2_ERR_INVALID_ARG", -2: "MIS2_ERR_OUT_OF_MEMORY", -3: "MIS2_ERR_CUDA",
+    -4: "MIS2_ERR_BAD_GRAPH", -5: "MIS2_ERR_TIMEOUT", -6: "MIS2_ERR_NO_PROGRESS",
+}
+MIS2_AGG_ALG3, MIS2_AGG_BASIC = 0, 1
+MIS2_HASH_XORSHIFT_STAR, MIS2_HASH_XORSHIFT, MIS2_HASH_FIXED = 0, 1, 2
+MIS2_LOOP_HOST, MIS2_LOOP_DEVICE = 0, 1
+MIS2_TRACE_CAP = 64
+MIS2_NUM_KERNEL_CLASSES = 8
+KERNEL_CLASSES = ["init", "column", "decide", "compact", "aggregate", "coarse", "device_loop", "other"]
+
+# C function names the header declares (checked by the CPU tests).
+EXPORTS = [
+    "mis2_config_default", "mis2_ctx_create", "mis2_ctx_destroy", "mis2_ctx_set_config", "mis2_get_stats",
+    "mis2_run", "mis2_run_with_priorities", "mis2_aggregate", "mis2_coarsen", "mis2_coarsen_level",
+    "mis2_coarsen_level_host", "mis2_status_string", "mis2_last_error", "mis2_version",
+]
+
+
+class Mis2Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        detail = ""
+        if status == -3:
+            try:
+                detail = ": " + _lib().mis2_last_error().decode()
+            except Exception:  # pragma: no cover
+                pass
+        super().__init__(f"{where} returned {STATUS.get(status, status)}{detail}")
+        self.status = status
+
+
+class mis2_csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr_is_64", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p)]
+
+
+class mis2_config(ctypes.Structure):
+    _fields_ = [("hash_variant", ctypes.c_int32), ("agg_mode", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
+                ("warp_degree", ctypes.c_int32), ("block_degree", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("loop", ctypes.c_int32), ("debug_checks", ctypes.c_int32), ("timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+
+
+class mis2_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("rounds2", ctypes.c_int32), ("n_roots", ctypes.c_int64),
+                ("n_phase1", ctypes.c_int64), ("n_aggs", ctypes.c_int64), ("c_nnz", ctypes.c_int64),
+                ("trace", (ctypes.c_int64 * 4) * MIS2_TRACE_CAP),
+                ("trace2", (ctypes.c_int64 * 4) * MIS2_TRACE_CAP),
+                ("kernel_ms", ctypes.c_double * MIS2_NUM_KERNEL_CLASSES),
+                ("kernel_launches", ctypes.c_int64 * MIS2_NUM_KERNEL_CLASSES),
+                ("launches", ctypes.c_int64)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def _lib(build_if_missing: bool = False):
+    """Load libmis2_gb300.so (raises if it is missing: no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"{path} is missing: build it with paper_2204_02934_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    CSR, CFG = ctypes.POINTER(mis2_csr), ctypes.POINTER(mis2_config)
+    pi64, pi32 = ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "mis2_config_default": (None, [CFG]),
+        "mis2_ctx_create": (i32, [ctypes.POINTER(P), i64, i64, CFG]),
+        "mis2_ctx_destroy": (i32, [P]),
+        "mis2_ctx_set_config": (i32, [P, CFG]),
+        "mis2_get_stats": (i32, [P, ctypes.POINTER(mis2_stats)]),
+        "mis2_run": (i32, [P, CSR, u64, P, P, pi64, pi32, P]),
+        "mis2_run_with_priorities": (i32, [P, CSR, P, i32, P, P, pi64, pi32, P]),
+        "mis2_aggregate": (i32, [P, CSR, P, i64, u64, i32, P, pi64, P]),
+        "mis2_coarsen": (i32, [P, CSR, P, i64, P, P, i64, pi64, P]),
+        "mis2_coarsen_level": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
+        "mis2_coarsen_level_host": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
+        "mis2_status_string": (ctypes.c_char_p, [i32]),
+        "mis2_last_error": (ctypes.c_char_p, []),
+        "mis2_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != MIS2_OK:
+        raise Mis2Error(rc, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------- C-ABI names
+def mis2_config_default() -> mis2_config:
+    cfg = mis2_config()
+    _lib().mis2_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def mis2_ctx_create(max_n: int, max_nnz: int, cfg: mis2_config | None = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(_lib().mis2_ctx_create(ctypes.byref(h), max_n, max_nnz, ctypes.byref(cfg) if cfg else None),
+           "mis2_ctx_create")
+    return h
+
+
+def mis2_ctx_destroy(ctx) -> None:
+    _check(_lib().mis2_ctx_destroy(ctx), "mis2_ctx_destroy")
+
+
+def mis2_ctx_set_config(ctx, cfg: mis2_config) -> None:
+    _check(_lib().mis2_ctx_set_config(ctx, ctypes.byref(cfg)), "mis2_ctx_set_config")
+
+
+def mis2_get_stats(ctx) -> mis2_stats:
+    st = mis2_stats()
+    _check(_lib().mis2_get_stats(ctx, ctypes.byref(st)), "mis2_get_stats")
+    return st
+
+
+def mis2_run(ctx, g: mis2_csr, seed: int, in_set, roots, stream=None):
+    """Returns (n_roots, n_rounds); in_set / roots are device tensors or None."""
+    nr, rounds = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(_lib().mis2_run(ctx, ctypes.byref(g), seed, _ptr(in_set), _ptr(roots), ctypes.byref(nr),
+                           ctypes.byref(rounds), _stream(stream)), "mis2_run")
+    return nr.value, rounds.value
+
+
+def mis2_run_with_priorities(ctx, g: mis2_csr, prio_table: np.ndarray, in_set, roots, stream=None):
+    tab = np.ascontiguousarray(prio_table, dtype=np.uint32)
+    nr, rounds = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(_lib().mis2_run_with_priorities(ctx, ctypes.byref(g), _ptr(tab), tab.shape[0], _ptr(in_set),
+                                           _ptr(roots), ctypes.byref(nr), ctypes.byref(rounds), _stream(stream)),
+           "mis2_run_with_priorities")
+    return nr.value, rounds.value
+
+
+def mis2_aggregate(ctx, g: mis2_csr, roots, n_roots: int, seed: int, mode: int, labels, stream=None) -> int:
+    na = ctypes.c_int64(0)
+    _check(_lib().mis2_aggregate(ctx, ctypes.byref(g), _ptr(roots), n_roots, seed, mode, _ptr(labels),
+                                 ctypes.byref(na), _stream(stream)), "mis2_aggregate")
+    return na.value
+
+
+def mis2_coarsen(ctx, g: mis2_csr, labels, n_aggs: int, c_rowptr, c_colind, c_colind_cap: int, stream=None) -> int:
+    cn = ctypes.c_int64(0)
+    _check(_lib().mis2_coarsen(ctx, ctypes.byref(g), _ptr(labels), n_aggs, _ptr(c_rowptr), _ptr(c_colind),
+                               c_colind_cap, ctypes.byref(cn), _stream(stream)), "mis2_coarsen")
+    return cn.value
+
+
+def mis2_coarsen_level(ctx, g: mis2_csr, seed: int, in_set, roots, labels, c_rowptr, c_colind, c_colind_cap: int,
+                       stream=None):
+    """Returns (n_roots, n_aggs, c_nnz)."""
+    nr, na, cn = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib().mis2_coarsen_level(ctx, ctypes.byref(g), seed, _ptr(in_set), _ptr(roots), _ptr(labels),
+                                     _ptr(c_rowptr), _ptr(c_colind), c_colind_cap, ctypes.byref(nr),
+                                     ctypes.byref(na), ctypes.byref(cn), _stream(stream)), "mis2_coarsen_level")
+    return nr.value, na.value, cn.value
+
+
+def mis2_coarsen_level_host(ctx, g_host: mis2_csr, seed: int, in_set, roots, labels, c_rowptr, c_colind,
+                            c_colind_cap: int, stream=None):
+    """Host-buffer variant (numpy arrays or pinned CPU tensors).  Returns
+    (n_roots, n_aggs, c_nnz)."""
+    nr, na, cn = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib().mis2_coarsen_level_host(ctx, ctypes.byref(g_host), seed, _ptr(in_set), _ptr(roots),
+                                          _ptr(labels), _ptr(c_rowptr), _ptr(c_colind), c_colind_cap,
+                                          ctypes.byref(nr), ctypes.byref(na), ctypes.byref(cn), _stream(stream)),
+           "mis2_coarsen_level_host")
+    return nr.value, na.value, cn.value
+
+
+def mis2_status_string(status: int) -> str:
+    return _lib().mis2_status_string(status).decode()
+
+
+def mis2_version() -> str:
+    return _lib().mis2_version().decode()
+
+
+# --------------------------------------------------------------- conveniences
+@dataclass
+class DeviceGraph:
+    """A CSR graph resident in device memory (torch tensors) and its C view."""
+
+    n: int
+    nnz: int
+    rowptr: object
+    colind: object
+
+    @property
+    def csr(self) -> mis2_csr:
+        import torch
+
+        return mis2_csr(self.n, self.nnz, 1 if self.rowptr.dtype == torch.int64 else 0, 0,
+                        self.rowptr.data_ptr(), self.colind.data_ptr() if self.nnz > 0 else None)
+
+    @staticmethod
+    def from_host(g, device="cuda") -> "DeviceGraph":
+        import torch
+
+        rp = torch.from_numpy(np.ascontiguousarray(g.rowptr)).to(device)
+        ci = torch.from_numpy(np.ascontiguousarray(g.colind, dtype=np.int32)).to(device)
+        if ci.numel() == 0:
+            ci = torch.zeros(4, dtype=torch.int32, device=device)
+        return DeviceGraph(int(g.n), int(g.colind.shape[0]), rp, ci)
+
+
+def host_csr(rowptr: np.ndarray, colind: np.ndarray, n: int) -> mis2_csr:
+    return mis2_csr(n, int(colind.shape[0]), 1 if rowptr.dtype == np.int64 else 0, 0,
+                    rowptr.ctypes.data, colind.ctypes.data if colind.shape[0] else None)
+
+
+class Context:
+    """Owns a mis2_ctx; methods allocate outputs as torch tensors."""
+
+    def __init__(self, max_n: int, max_nnz: int, cfg: mis2_config | None = None, **overrides):
+        cfg = cfg or mis2_config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.max_n, self.max_nnz = max_n, max_nnz
+        self.handle = mis2_ctx_create(max_n, max_nnz, cfg)
+
+    def close(self):
+        if self.handle:
+            mis2_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, **overrides):
+        for k, v in overrides.items():
+            setattr(self.cfg, k, v)
+        mis2_ctx_set_config(self.handle, self.cfg)
+
+    def stats(self) -> mis2_stats:
+        return mis2_get_stats(self.handle)
+
+    def run(self, dg: DeviceGraph, seed: int = 0, stream=None):
+        import torch
+
+        in_set = torch.empty(max(dg.n, 1), dtype=torch.uint8, device=dg.rowptr.device)
+        roots = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.rowptr.device)
+        nr, rounds = mis2_run(self.handle, dg.csr, seed, in_set, roots, stream)
+        return in_set[:dg.n], roots[:nr], rounds
+
+    def run_with_priorities(self, dg: DeviceGraph, prio_table, stream=None):
+        import torch
+
+        in_set = torch.empty(max(dg.n, 1), dtype=torch.uint8, device=dg.rowptr.device)
+        roots = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.rowptr.device)
+        nr, rounds = mis2_run_with_priorities(self.handle, dg.csr, prio_table, in_set, roots, stream)
+        return in_set[:dg.n], roots[:nr], rounds
+
+    def aggregate(self, dg: DeviceGraph, roots, seed: int = 0, mode: int = MIS2_AGG_ALG3, stream=None):
+        import torch
+
+        labels = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.rowptr.device)
+        na = mis2_aggregate(self.handle, dg.csr, roots, int(roots.numel()), seed, mode, labels, stream)
+        return labels[:dg.n], na
+
+    def coarsen(self, dg: DeviceGraph, labels, n_aggs: int, stream=None):
+        import torch
+
+        c_rowptr = torch.empty(n_aggs + 1, dtype=torch.int32, device=dg.rowptr.device)
+        cap = max(dg.nnz, 1)
+        c_colind = torch.empty(cap, dtype=torch.int32, device=dg.rowptr.device)
+        cn = mis2_coarsen(self.handle, dg.csr, labels, n_aggs, c_rowptr, c_colind, cap, stream)
+        return c_rowptr, c_colind[:cn]
+
+    def coarsen_level(self, dg: DeviceGraph, seed: int = 0, stream=None):
+        import torch
+
+        dev = dg.rowptr.device
+        in_set = torch.empty(max(dg.n, 1), dtype=torch.uint8, device=dev)
+        roots = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dev)
+        labels = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dev)
+        c_rowptr = torch.empty(dg.n + 1, dtype=torch.int32, device=dev)
+        cap = max(dg.nnz, 1)
+        c_colind = torch.empty(cap, dtype=torch.int32, device=dev)
+        nr, na, cn = mis2_coarsen_level(self.handle, dg.csr, seed, in_set, roots, labels, c_rowptr, c_colind, cap,
+                                        stream)
+        return dict(in_set=in_set[:dg.n], roots=roots[:nr], labels=labels[:dg.n], n_aggs=na,
+                    c_rowptr=c_rowptr[:na + 1], c_colind=c_colind[:cn])

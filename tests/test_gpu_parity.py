@@ -1,0 +1,242 @@
+"""Bit-exact parity of the CUDA library (through the C ABI) with the CPU
+oracle: MIS-2 flags, roots, round counts and per-round worklist traces,
+aggregate labels and the coarse CSR, on seeded graphs shaped like the
+workloads, edge cases, and every row mapping / loop driver."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_02934_gb300 import graphgen as gg
+from paper_2204_02934_gb300 import mis2
+from _gpu import assert_level_equal, gpu_level, make_ctx
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+LOOPS = [mis2.MIS2_LOOP_HOST, mis2.MIS2_LOOP_DEVICE]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_02934_gb300 import _build
+
+    _build.build()
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_fig1_worked_example_on_gpu(loop):
+    """Section III-A, Fig. 1 through the priority-injection hook."""
+    fx = json.load(open(os.path.join(GOLDEN, "fig1.json")))
+    n = fx["n"]
+    g = gg.graph_from_edges(n, [(a - 1, b - 1) for a, b in fx["edges"]])
+    tab = np.zeros((len(fx["rounds"]), n), dtype=np.uint32)
+    for r, rd in enumerate(fx["rounds"]):
+        for vid, p in rd["priorities"].items():
+            tab[r, int(vid) - 1] = p
+    ctx = make_ctx(g, loop=loop)
+    in_set, roots, rounds = ctx.run_with_priorities(mis2.DeviceGraph.from_host(g), tab)
+    assert (roots.cpu().numpy() + 1).tolist() == fx["result"]
+    assert rounds == fx["n_rounds"]
+
+
+def _edges_of(n, mask):
+    pairs = list(itertools.combinations(range(n), 2))
+    return [p for k, p in enumerate(pairs) if (mask >> k) & 1]
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_exhaustive_small_graphs(loop):
+    """Every labelled graph on 5 vertices, both aggregation modes."""
+    n = 5
+    ctxs = {m: mis2.Context(8, 32, loop=loop, agg_mode=m) for m in (0, 1)}
+    for mask in range(1 << 10):
+        g = gg.graph_from_edges(n, _edges_of(n, mask))
+        for mode in (0, 1):
+            assert_level_equal(g, gpu_level(ctxs[mode], g, seed=mask), seed=mask, mode=mode)
+
+
+def _graphs():
+    yield "gnp200", gg.random_graph(200, 0.03, 1)
+    yield "gnp500", gg.random_graph(500, 0.01, 2)
+    yield "grid2d_37x29", gg.grid2d_5pt(37, 29)
+    yield "grid3d7_13", gg.grid3d_7pt(13, 11, 9)
+    yield "grid3d27_17", gg.grid3d_27pt(17, 15, 13)
+    yield "rgg3000", gg.rgg2d(3000, 10.0, 4)
+    yield "rmat12", gg.rmat(12, 8, seed=5)
+    yield "rmat12_i32", gg.rmat(12, 8, seed=6, rowptr_dtype=np.int32)
+    yield "elasticity5", gg.elasticity3d(5, 4, 3)
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name,g", list(_graphs()))
+def test_parity_graphs(name, g, mode, loop):
+    ctx = make_ctx(g, loop=loop, agg_mode=mode)
+    for seed in (0, 7):
+        assert_level_equal(g, gpu_level(ctx, g, seed), seed=seed, mode=mode)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("loop", LOOPS)
+def test_every_row_mapping(lanes, loop):
+    """Group sizes, warp rows and block rows all give the same bits: low
+    thresholds push rows of the R-MAT graph into every class."""
+    g = gg.rmat(11, 8, seed=9)
+    ctx = make_ctx(g, loop=loop, group_lanes=lanes, warp_degree=8, block_degree=64)
+    assert_level_equal(g, gpu_level(ctx, g, 3), seed=3)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_hash_variants(variant):
+    g = gg.grid3d_7pt(12, 12, 12)
+    ctx = make_ctx(g, hash_variant=variant)
+    lv = oracle.coarsen_level(g, seed=0, hash_variant=variant, trace_cap=mis2.MIS2_TRACE_CAP)
+    out = gpu_level(ctx, g, 0)
+    assert np.array_equal(out["roots"], lv.roots) and out["rounds"] == lv.rounds
+    assert np.array_equal(out["labels"], lv.labels)
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_edge_cases(loop):
+    cases = [
+        gg.graph_from_edges(1, []),
+        gg.graph_from_edges(7, []),                                   # isolated vertices
+        gg.graph_from_edges(2, [(0, 1)]),
+        gg.graph_from_edges(9, list(itertools.combinations(range(9), 2))),  # clique
+        gg.graph_from_edges(300, [(i, i + 1) for i in range(299)]),   # path
+        gg.graph_from_edges(5000, [(0, i) for i in range(1, 5000)]),  # star: one block row
+        gg.graph_from_edges(40, [(0, i) for i in range(1, 20)] + [(20, i) for i in range(21, 40)] + [(5, 25)]),
+    ]
+    for g in cases:
+        ctx = make_ctx(g, loop=loop, block_degree=1024, warp_degree=16)
+        assert_level_equal(g, gpu_level(ctx, g, 1), seed=1)
+
+
+def test_empty_graph():
+    g = gg.graph_from_edges(0, [])
+    ctx = mis2.Context(1, 1)
+    dg = mis2.DeviceGraph.from_host(g)
+    in_set, roots, rounds = ctx.run(dg)
+    assert roots.numel() == 0 and rounds == 0
+
+
+def _with_extra_entries(g, duplicates):
+    rp = g.rowptr.astype(np.int64)
+    rows, cols = [], []
+    for v in range(g.n):
+        row = list(g.colind[rp[v]:rp[v + 1]])
+        cs = row + [v] + (row[:1] if duplicates else [])
+        rows.append(len(cs))
+        cols.extend(cs)
+    rp2 = np.concatenate([[0], np.cumsum(rows)]).astype(np.int64)
+    return gg.CSRGraph(g.n, rp2, np.asarray(cols, dtype=np.int32))
+
+
+def test_self_loops_duplicates_and_unaligned_colind():
+    """Stored diagonals (and, for MIS-2, duplicate entries) change nothing; a
+    colind that is only 4-byte aligned takes the scalar-load path with the
+    same result."""
+    import torch
+
+    base = gg.random_graph(300, 0.02, 8)
+    for dup in (False, True):
+        g2 = _with_extra_entries(base, dup)
+        ctx = make_ctx(g2)
+        buf = torch.zeros(g2.nnz + 1, dtype=torch.int32, device="cuda")
+        buf[1:] = torch.from_numpy(g2.colind).cuda()
+        dg = mis2.DeviceGraph(g2.n, g2.nnz, torch.from_numpy(g2.rowptr).cuda(), buf[1:])
+        in_set, roots, rounds = ctx.run(dg, 2)
+        ref = oracle.mis2(g2, seed=2)
+        assert np.array_equal(roots.cpu().numpy(), ref[1]) and rounds == ref[2]
+        if not dup:
+            out = ctx.coarsen_level(dg, 2)
+            lv = oracle.coarsen_level(g2, seed=2)
+            assert np.array_equal(out["labels"].cpu().numpy(), lv.labels)
+            assert np.array_equal(out["c_colind"].cpu().numpy(), lv.c_colind)
+
+
+def test_separate_calls_match_level_call():
+    """mis2_run -> mis2_aggregate -> mis2_coarsen equals mis2_coarsen_level."""
+    g = gg.grid3d_27pt(20, 18, 16)
+    ctx = make_ctx(g)
+    dg = mis2.DeviceGraph.from_host(g)
+    in_set, roots, rounds = ctx.run(dg, 5)
+    labels, na = ctx.aggregate(dg, roots, 5)
+    c_rowptr, c_colind = ctx.coarsen(dg, labels, na)
+    ref = oracle.coarsen_level(g, seed=5)
+    assert np.array_equal(roots.cpu().numpy(), ref.roots)
+    assert np.array_equal(labels.cpu().numpy(), ref.labels)
+    assert np.array_equal(c_colind.cpu().numpy(), ref.c_colind)
+
+
+def test_host_buffer_entry_point():
+    g = gg.grid3d_7pt(30, 30, 30)
+    ctx = make_ctx(g)
+    n = g.n
+    in_set = np.zeros(n, np.uint8)
+    roots = np.zeros(n, np.int32)
+    labels = np.zeros(n, np.int32)
+    c_rowptr = np.zeros(n + 1, np.int32)
+    c_colind = np.zeros(g.nnz, np.int32)
+    rp = np.ascontiguousarray(g.rowptr)
+    ci = np.ascontiguousarray(g.colind)
+    nr, na, cn = mis2.mis2_coarsen_level_host(ctx.handle, mis2.host_csr(rp, ci, n), 3, in_set, roots, labels,
+                                              c_rowptr, c_colind, g.nnz)
+    ref = oracle.coarsen_level(g, seed=3)
+    assert np.array_equal(roots[:nr], ref.roots) and np.array_equal(labels, ref.labels)
+    assert np.array_equal(c_rowptr[:na + 1].astype(np.int64), ref.c_rowptr)
+    assert np.array_equal(c_colind[:cn], ref.c_colind)
+
+
+def test_determinism_and_loop_drivers_agree():
+    g = gg.rmat(13, 8, seed=2)
+    outs = []
+    for loop in LOOPS * 2:
+        ctx = make_ctx(g, loop=loop)
+        outs.append(gpu_level(ctx, g, 11))
+    for o in outs[1:]:
+        for k in ("labels", "c_colind", "roots"):
+            assert np.array_equal(o[k], outs[0][k])
+
+
+def test_invalid_arguments():
+    g = gg.grid2d_5pt(10, 10)
+    ctx = make_ctx(g)
+    big = gg.grid2d_5pt(20, 20)
+    dg = mis2.DeviceGraph.from_host(big)
+    with pytest.raises(mis2.Mis2Error) as e:
+        ctx.run(dg)
+    assert e.value.status == -2  # larger than the context
+    with pytest.raises(mis2.Mis2Error):
+        mis2.Context(10, 10, group_lanes=3)
+
+
+# ---------------------------------------------------------------- workloads
+@pytest.mark.parametrize("loop", LOOPS)
+def test_workload_small_5pt_100x100(loop):
+    g = gg.workload_small()
+    assert g.n == 10_000 and g.nnz == 39_600
+    ctx = make_ctx(g, loop=loop)
+    assert_level_equal(g, gpu_level(ctx, g, 0), seed=0)
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_workload_27pt_100(loop):
+    g = gg.workload_27pt(100)
+    assert g.nnz == 25_463_592
+    ctx = make_ctx(g, loop=loop)
+    assert_level_equal(g, gpu_level(ctx, g, 0), seed=0)
+
+
+def test_workload_rmat_scale22():
+    g = gg.workload_rmat(22)
+    assert g.rowptr.dtype == np.int64
+    ctx = make_ctx(g, loop=mis2.MIS2_LOOP_DEVICE)
+    assert_level_equal(g, gpu_level(ctx, g, 0), seed=0)

@@ -176,21 +176,34 @@ def test_degenerate_graphs():
     assert len(roots) == 1
 
 
-def test_self_loops_and_duplicates_are_harmless():
-    """Closed neighbourhoods: a stored diagonal or duplicate entry changes no
-    min / any / all, so the result equals that of the clean graph."""
-    g = gg.random_graph(80, 0.05, 3)
+def _with_extra_entries(g, self_loops=True, duplicates=True):
     rp = g.rowptr.astype(np.int64)
     rows, cols = [], []
     for v in range(g.n):
-        cs = list(g.colind[rp[v]:rp[v + 1]]) + [v] + list(g.colind[rp[v]:rp[v + 1]][:1])
+        row = list(g.colind[rp[v]:rp[v + 1]])
+        cs = row + ([v] if self_loops else []) + (row[:1] if duplicates else [])
         rows.append(len(cs))
         cols.extend(cs)
     rp2 = np.concatenate([[0], np.cumsum(rows)]).astype(np.int64)
-    g2 = gg.CSRGraph(g.n, rp2, np.asarray(cols, dtype=np.int32))
+    return gg.CSRGraph(g.n, rp2, np.asarray(cols, dtype=np.int32))
+
+
+def test_self_loops_and_duplicates_are_harmless():
+    """Closed neighbourhoods: a stored diagonal or a duplicate entry changes
+    no min / any / all of Algorithm 1.  Aggregation counts neighbours (the
+    >= 2 test of phase 2, coupling in phase 3) over the edge set, so there a
+    row may hold a self-loop but must list each neighbour once."""
+    g = gg.random_graph(80, 0.05, 3)
+    g2 = _with_extra_entries(g)
     a = oracle.mis2(g, seed=5)
     b = oracle.mis2(g2, seed=5)
     assert (a[0] == b[0]).all() and a[2] == b[2]
+    g3 = _with_extra_entries(g, duplicates=False)
+    for mode in (0, 1):
+        la = oracle.coarsen_level(g, seed=5, mode=mode)
+        lb = oracle.coarsen_level(g3, seed=5, mode=mode)
+        assert (la.labels == lb.labels).all() and la.n_aggs == lb.n_aggs
+        assert (la.c_rowptr == lb.c_rowptr).all() and (la.c_colind == lb.c_colind).all()
 
 
 def test_path_graph_closed_form():
