@@ -207,6 +207,32 @@ int mis2_coarsen_level_host(mis2_ctx* ctx, const mis2_csr* g_host, uint64_t seed
                             int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                             int64_t* n_aggs, int64_t* c_nnz, void* stream);
 
+/*
+ * MIS-2 without allocating: the same result as mis2_run (and the same
+ * arguments, minus the context), for callers that cannot call cudaMalloc --
+ * processes whose device memory is fully budgeted up front, or whose
+ * allocator owns the whole device, and latency-critical code that must not
+ * block on cudaMalloc / cudaFree.  The paper has no counterpart; this is a
+ * deployment variant of Algorithm 1's driver.
+ *
+ * Scratch comes from a fixed array of about 14.7 MB compiled into the
+ * library, present on every GPU that loads the library until the process
+ * exits.  Graphs with more than MIS2_NOALLOC_MAX_N vertices are rejected with
+ * MIS2_ERR_INVALID_ARG (message in mis2_last_error()); nnz is not limited,
+ * since colind stays in caller memory.  No cudaMalloc, cudaFree or other
+ * allocating call is made: host-side counters use stack memory.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any CUDA
+ * stream capture.  All calls share the array, so calls that overlap on the
+ * GPU (concurrent streams or threads) race and give wrong results; serialise
+ * them.  The round loop runs on the device (MIS2_LOOP_DEVICE) with the
+ * default configuration.  Synchronises `stream`.
+ */
+#define MIS2_NOALLOC_MAX_N 262144
+int mis2_run_noalloc(const mis2_csr* g, uint64_t seed, uint8_t* in_set, int32_t* roots,
+                     int64_t* n_roots, int32_t* n_rounds, void* stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* mis2_status_string(int status);
 

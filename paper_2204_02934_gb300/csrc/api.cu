@@ -17,6 +17,8 @@ int set_cuda_error(cudaError_t e) {
   return MIS2_ERR_CUDA;
 }
 
+void set_error_text(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 void timer_begin(mis2_ctx* c, int cls, cudaStream_t st) {
   if (!c->cfg.timing) return;
   Timer& t = c->timer;

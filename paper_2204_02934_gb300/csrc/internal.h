@@ -121,6 +121,7 @@ struct GraphArgs {
 };
 
 int set_cuda_error(cudaError_t e);
+void set_error_text(const char* msg);
 #define MIS2_CUDA(call)                                     \
   do {                                                      \
     cudaError_t _e = (call);                                \

@@ -33,8 +33,9 @@ KERNEL_CLASSES = ["init", "column", "decide", "compact", "aggregate", "coarse", 
 EXPORTS = [
     "mis2_config_default", "mis2_ctx_create", "mis2_ctx_destroy", "mis2_ctx_set_config", "mis2_get_stats",
     "mis2_run", "mis2_run_with_priorities", "mis2_aggregate", "mis2_coarsen", "mis2_coarsen_level",
-    "mis2_coarsen_level_host", "mis2_status_string", "mis2_last_error", "mis2_version",
+    "mis2_coarsen_level_host", "mis2_status_string", "mis2_last_error", "mis2_version", "mis2_run_noalloc",
 ]
+MIS2_NOALLOC_MAX_N = 262144
 
 
 class Mis2Error(RuntimeError):
@@ -105,6 +106,7 @@ def _lib(build_if_missing: bool = False):
         "mis2_coarsen": (i32, [P, CSR, P, i64, P, P, i64, pi64, P]),
         "mis2_coarsen_level": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
         "mis2_coarsen_level_host": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
+        "mis2_run_noalloc": (i32, [CSR, u64, P, P, pi64, pi32, P]),
         "mis2_status_string": (ctypes.c_char_p, [i32]),
         "mis2_last_error": (ctypes.c_char_p, []),
         "mis2_version": (ctypes.c_char_p, []),
@@ -219,6 +221,16 @@ def mis2_coarsen_level_host(ctx, g_host: mis2_csr, seed: int, in_set, roots, lab
                                           ctypes.byref(nr), ctypes.byref(na), ctypes.byref(cn), _stream(stream)),
            "mis2_coarsen_level_host")
     return nr.value, na.value, cn.value
+
+
+def mis2_run_noalloc(g: mis2_csr, seed: int, in_set, roots, stream=None):
+    """MIS-2 through the entry point that allocates nothing (for callers that
+    cannot call cudaMalloc); graphs up to MIS2_NOALLOC_MAX_N vertices.
+    Returns (n_roots, n_rounds)."""
+    nr, rounds = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(_lib().mis2_run_noalloc(ctypes.byref(g), seed, _ptr(in_set), _ptr(roots), ctypes.byref(nr),
+                                   ctypes.byref(rounds), _stream(stream)), "mis2_run_noalloc")
+    return nr.value, rounds.value
 
 
 def mis2_status_string(status: int) -> str:
