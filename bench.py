@@ -320,6 +320,8 @@ def run_ours(args):
             "kernel_ms_per_step": breakdown,
             "clocks": ck,
             "mis2": {"n_roots": int(nr), "n_aggs": int(na), "c_nnz": int(cn)}}
+    if not args.no_batch:
+        line["batched_vs_plain"] = run_batch_compare()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(g, args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -327,6 +329,79 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_batch_compare(steps=3, warmup=2, n_graphs=512, seed=7, min_n=1000):
+    """Batched hierarchies vs per-graph plain launches on the mixed-size batch
+    (2D 5-pt / 3D 7-pt / 2D RGG, 1k-200k vertices, log-uniform), each graph
+    coarsened recursively until it has fewer than min_n vertices.
+    Returns a dict with graphs/s of both paths and the identity check."""
+    import torch
+
+    from paper_2204_02934_gb300 import graphgen as gg, mis2
+
+    graphs = gg.mixed_batch(n_graphs, seed=seed)
+    tot_n, tot_nnz = sum(g.n for g in graphs), sum(g.nnz for g in graphs)
+    dgs = [mis2.DeviceGraph.from_host(g) for g in graphs]
+    b = mis2.Batch(n_graphs, tot_n, tot_nnz, loop=mis2.MIS2_LOOP_DEVICE)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(max(warmup, 1)):
+        nlev = b.coarsen(dgs, min_n=min_n)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_b = 0.0
+    launches = 0
+    for _ in range(steps):
+        flush.fill_(1)
+        ev0.record()
+        nlev = b.coarsen(dgs, min_n=min_n)
+        ev1.record()
+        ev1.synchronize()
+        t_b += ev0.elapsed_time(ev1) / 1e3
+        launches += b.stats().launches
+    batched = n_graphs * steps / t_b
+
+    # per-graph plain launches: host-driven rounds, one graph and one level at a time
+    maxn = max(g.n for g in graphs)
+    maxnnz = max(g.nnz for g in graphs)
+    ctx = mis2.Context(maxn, maxnnz, loop=mis2.MIS2_LOOP_HOST)
+
+    def plain_pass(record=False):
+        out = []
+        for dg in dgs:
+            cur, levels = dg, []
+            while cur.n >= min_n and len(levels) < 32:
+                r = ctx.coarsen_level(cur, 0)
+                levels.append(r["labels"] if record else None)
+                if r["n_aggs"] >= cur.n:
+                    break
+                cur = mis2.DeviceGraph(r["n_aggs"], int(r["c_colind"].numel()), r["c_rowptr"],
+                                       r["c_colind"] if r["c_colind"].numel() else torch.zeros(4, dtype=torch.int32,
+                                                                                             device="cuda"))
+            out.append(levels)
+        return out
+
+    ref = plain_pass(record=True)
+    torch.cuda.synchronize()
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_pass()
+    torch.cuda.synchronize()
+    t_p = time.perf_counter() - t0
+    plain = n_graphs / t_p
+    same = True
+    for gi in range(n_graphs):
+        for L, lab in enumerate(ref[gi]):
+            if not torch.equal(b.labels(L, gi), lab):
+                same = False
+                break
+        if not same:
+            break
+    return {"workload": f"{n_graphs} mixed graphs (2D 5-pt, 3D 7-pt, 2D RGG; 1k-200k vertices, log-uniform, "
+                        f"{tot_n} vertices, {tot_nnz} entries), recursive coarsening until < {min_n} vertices",
+            "unit": "graphs/s", "batched": batched, "plain": plain, "speedup": batched / plain,
+            "levels": nlev, "identical_output": same, "batched_ms": 1e3 * t_b / steps,
+            "plain_ms": 1e3 * t_p, "batched_gpu_launches_per_step": launches // steps}
 
 
 def _traffic_from_profile(kernel):
@@ -359,6 +434,7 @@ def main():
     ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat"])
     ap.add_argument("--loop", default="device", choices=["device", "host"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -83,13 +83,13 @@ typedef struct {
   int32_t hash_variant;   /* MIS2_HASH_*; default XORSHIFT_STAR */
   int32_t agg_mode;       /* MIS2_AGG_*; default ALG3 */
   int32_t group_lanes;    /* lanes per low-degree row: 0 = pick from average degree, else 1,2,4,8,16,32 */
-  int32_t warp_degree;    /* rows with degree >= this get a full warp (default 64) */
+  int32_t warp_degree;    /* rows with degree >= this get a full warp (default 32) */
   int32_t block_degree;   /* rows with degree >= this get a full block (default 2048) */
   int32_t block_size;     /* threads per block for row kernels (default 256) */
   int32_t loop;           /* MIS2_LOOP_*; default DEVICE */
   int32_t debug_checks;   /* validate CSR and roots (extra passes); default 0 */
   int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
-  int32_t reserved;
+  int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = as many as fit (max 4) */
   int64_t spin_limit;     /* polls before a device barrier reports MIS2_ERR_TIMEOUT */
 } mis2_config;
 
@@ -206,6 +206,100 @@ int mis2_coarsen_level_host(mis2_ctx* ctx, const mis2_csr* g_host, uint64_t seed
                             uint8_t* in_set, int32_t* roots, int32_t* labels, int32_t* c_rowptr,
                             int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                             int64_t* n_aggs, int64_t* c_nnz, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched hierarchies: many graphs, every level of their recursive
+ * coarsening (Section I: multilevel methods coarsen recursively until the
+ * graph is below a threshold), processed together.  Each level of all live
+ * graphs runs as one block-diagonal union: one persistent launch per MIS-2
+ * for every graph's rounds, aggregation and coarse graph on the union.  Every
+ * graph's results are bit-identical to coarsening it alone with
+ * mis2_coarsen_level, level after level.
+ * ------------------------------------------------------------------------ */
+typedef struct mis2_batch mis2_batch;
+
+/* Scratch for up to max_graphs graphs totalling max_total_n vertices and
+ * max_total_nnz entries at level 0 (allocated now; per-level outputs are
+ * allocated on first use and reused by later runs of the same sizes). */
+int mis2_batch_create(mis2_batch** b, int32_t max_graphs, int64_t max_total_n, int64_t max_total_nnz,
+                      const mis2_config* cfg);
+int mis2_batch_destroy(mis2_batch* b);
+
+/*
+ * Coarsen each graph (graphs: HOST array of n_graphs mis2_csr whose rowptr /
+ * colind are device pointers; rows must list each neighbour once) level
+ * after level while it has >= min_n vertices and keeps shrinking, for at most
+ * max_levels levels.  *n_levels (host) receives the number of levels built.
+ * Synchronises `stream`.
+ */
+int mis2_batch_coarsen(mis2_batch* b, int32_t n_graphs, const mis2_csr* graphs, uint64_t seed, int64_t min_n,
+                       int32_t max_levels, int32_t* n_levels, void* stream);
+
+/* Sizes at `level`: n[g] vertices, n_aggs[g] aggregates and c_nnz[g] coarse
+ * entries of graph g (host arrays of n_graphs, each may be NULL; 0 for
+ * graphs not coarsened at that level). */
+int mis2_batch_level_sizes(const mis2_batch* b, int32_t level, int64_t* n, int64_t* n_aggs, int64_t* c_nnz);
+
+/* Aggregate labels of graph `graph` at `level` (device int32[n], values in
+ * [0, n_aggs)); MIS2_ERR_INVALID_ARG if the graph was not coarsened there. */
+int mis2_batch_labels(const mis2_batch* b, int32_t level, int32_t graph, int32_t* labels, void* stream);
+
+/* Coarse graph of graph `graph` built at `level` (device int32[n_aggs+1]
+ * and int32[c_colind_cap >= c_nnz]); the same graph is the input of
+ * level + 1.  Synchronises `stream`. */
+int mis2_batch_coarse(const mis2_batch* b, int32_t level, int32_t graph, int32_t* c_rowptr, int32_t* c_colind,
+                      int64_t c_colind_cap, void* stream);
+
+/* Statistics of the last mis2_batch_coarsen (launch count, kernel times). */
+int mis2_batch_stats(const mis2_batch* b, mis2_stats* out);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Each request is one
+ * coarsening level (mis2_coarsen_level_host) of a graph in HOST memory.
+ * Requests queue in arrival order and are admitted while an execution slot
+ * is free and the device-memory budget holds their buffers; each slot owns a
+ * resident context (status arrays, worklists, staging buffers), a stream and
+ * a host thread, so requests admitted while others run overlap on the GPU.
+ * Results are independent of the mix (every slot has its own scratch).
+ * ------------------------------------------------------------------------ */
+typedef struct mis2_server mis2_server;
+
+typedef struct {
+  int32_t slots;          /* concurrent requests (default 4) */
+  int32_t reserved;
+  int64_t mem_budget;     /* bytes of request buffers admitted at once (default 8 GiB) */
+  int64_t slot_max_n;     /* largest request per slot (vertices, entries) */
+  int64_t slot_max_nnz;
+  mis2_config cfg;        /* per-slot configuration (default loop: MIS2_LOOP_HOST) */
+} mis2_server_config;
+
+typedef struct {
+  int64_t ticket;
+  int64_t n, nnz;
+  int64_t n_roots, n_aggs, c_nnz;
+  uint64_t checksum;        /* FNV-1a over roots, labels, coarse rowptr and colind */
+  double t_arrive, t_start, t_done;  /* seconds since the server was created */
+  int32_t status;           /* mis2_status of the request */
+  int32_t slot;
+} mis2_result;
+
+void mis2_server_config_default(mis2_server_config* cfg);
+/* Creates cfg->slots contexts (cudaMalloc now) and their worker threads. */
+int mis2_server_create(mis2_server** s, const mis2_server_config* cfg);
+/* Stops the workers after the queue drains, frees everything. */
+int mis2_server_destroy(mis2_server* s);
+/* Queue one request; g_host points to HOST memory that must stay valid until
+ * the request completes.  *ticket (host) identifies it.  Does not block. */
+int mis2_server_submit(mis2_server* s, const mis2_csr* g_host, uint64_t seed, int64_t* ticket);
+/* Block until request `ticket` completes; *out (host) receives its result. */
+int mis2_server_wait(mis2_server* s, int64_t ticket, mis2_result* out);
+/* Replay an arrival trace: request i (graph pool_host[pool_index[i]])
+ * arrives arrival_s[i] seconds after the call starts; results[i] (host)
+ * receive the outcomes, *max_in_flight the peak number of concurrent
+ * requests.  Blocks until all complete. */
+int mis2_server_replay(mis2_server* s, int32_t n_pool, const mis2_csr* pool_host, int64_t n_req,
+                       const double* arrival_s, const int32_t* pool_index, uint64_t seed, mis2_result* results,
+                       int64_t* max_in_flight);
 
 /*
  * MIS-2 without allocating: the same result as mis2_run (and the same

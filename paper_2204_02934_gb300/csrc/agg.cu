@@ -9,6 +9,7 @@
 // Aggregate ids: phase-1 roots in ascending order, then qualifying phase-2
 // roots in ascending order.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 #include "mis_rows.cuh"
@@ -16,7 +17,8 @@
 namespace mis2 {
 
 constexpr int kErrNoAggregatedNeighbour = 2;
-constexpr int kPhase3Window = 8192;
+constexpr int kPhase3Window = 8192;   // aggregate ids counted per pass for the heaviest rows
+constexpr int kPhase3SortCap = 8192;  // rows up to this length are sorted in shared memory
 
 // Root list entry j claims itself and every neighbour still labelled -1 for
 // aggregate base + j.  Roots are more than two hops apart (in the graph, or
@@ -94,23 +96,26 @@ __global__ void __launch_bounds__(kBlock) k_aggsize(int64_t n, const int32_t* te
   }
 }
 
-// Leftovers of phases 1-2, split by degree (block rows go to `heavy`).
+// Leftovers of phases 1-2, split by degree: short rows (<= kLaneRowMax
+// entries) to `left`, medium rows to `mid`, rows above kPhase3SortCap to
+// `heavy`.
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_leftovers(GraphView<I> g, const int32_t* tent, int32_t* left,
-                                                      int32_t* left_cnt, int32_t* heavy, int32_t* heavy_cnt,
-                                                      int32_t block_degree) {
+                                                      int32_t* left_cnt, int32_t* mid, int32_t* mid_cnt,
+                                                      int32_t* heavy, int32_t* heavy_cnt) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = lane_id();
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < g.n; base += stride) {
     const int64_t v = base + lane;
-    bool lo = false, hi = false;
+    int cls = -1;
     if (v < g.n && tent[v] == -1) {
       int64_t s, e;
       row_range(g, v, s, e);
-      (e - s >= block_degree ? hi : lo) = true;
+      cls = e - s <= kLaneRowMax ? 0 : (e - s <= kPhase3SortCap ? 1 : 2);
     }
-    warp_append(lo, (int32_t)v, left, left_cnt);
-    warp_append(hi, (int32_t)v, heavy, heavy_cnt);
+    warp_append(cls == 0, (int32_t)v, left, left_cnt);
+    warp_append(cls == 1, (int32_t)v, mid, mid_cnt);
+    warp_append(cls == 2, (int32_t)v, heavy, heavy_cnt);
   }
 }
 
@@ -118,64 +123,146 @@ __device__ __forceinline__ bool better(int c, int sz, int a, int bc, int bs, int
   return ba < 0 || c > bc || (c == bc && (sz < bs || (sz == bs && a < ba)));
 }
 
-// Phase 3, group of G lanes per leftover: visit the adjacent aggregates in
-// increasing id order (one min-reduction per distinct id), count coupling
-// for each, keep the best by (max coupling, min size, min id).
-template <int G, typename I>
-__global__ void __launch_bounds__(kBlock) k_phase3(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
-                                                   const int32_t* left, const int32_t* left_cnt, int32_t* labels,
-                                                   int32_t* err) {
-  constexpr int RPW = 32 / G;
+// Phase 3, one lane per short leftover row: stage the row, gather its
+// neighbours' tentative labels into the lane's own shared-memory slot, and
+// pick the best adjacent aggregate by (max coupling, min size, min id).
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
+                                                        const int32_t* left, const int32_t* left_cnt, int32_t* labels,
+                                                        int32_t* err) {
+  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  const int lane = lane_id();
+  int4* my = stage[threadIdx.x >> 5] + lane * kStageInt4;
+  int32_t* myw = reinterpret_cast<int32_t*>(my);
   const int64_t cnt = *left_cnt;
-  const int lane = lane_id(), lg = lane & (G - 1), sub = lane / G;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * RPW; base < cnt; base += nw * RPW) {
-    const int64_t i = base + sub;
+  for (int64_t base = warp * 32; base < cnt; base += nw * 32) {
+    const int64_t i = base + lane;
     const bool active = i < cnt;
     int32_t v = 0;
     int64_t s = 0, e = 0;
+    int off = -1;
     if (active) {
       v = left[i];
       row_range(g, v, s, e);
+      off = stage_row(g, s, e, my);
     }
-    bool done = !active;
-    int32_t last = -1, best = -1;
+    cp_async_wait_all();
+    if (!active) continue;
+    const int len = (int)(e - s);
+    int32_t lab[kLaneRowMax];
+#pragma unroll
+    for (int j = 0; j < kLaneRowMax; j++) {
+      int32_t t = -1;
+      if (j < len) {
+        const int32_t w = off >= 0 ? myw[off + j] : g.colind[s + j];
+        t = w != v ? tent[w] : -1;
+      }
+      lab[j] = t;
+    }
+#pragma unroll
+    for (int j = 0; j < kLaneRowMax; j++) myw[j] = lab[j];  // own slot only: no other lane reads it
+    int32_t best = -1;
     int bc = 0, bs = 0;
-    while (__any_sync(kFull, !done)) {
-      uint32_t a = 0xFFFFFFFFu;
-      if (!done)
-        visit_row<G>(g.colind, g.nnz, s, e, lg, g.vec, [&](int32_t w) {
-          const int32_t t = tent[w];
-          if (w != v && t > last && (uint32_t)t < a) a = (uint32_t)t;
-        });
-      a = group_min<G>(a);
-      int c = 0;
-      if (!done && a != 0xFFFFFFFFu)
-        visit_row<G>(g.colind, g.nnz, s, e, lg, g.vec, [&](int32_t w) { c += (w != v && tent[w] == (int32_t)a); });
-      c = group_sum<G>(c);
-      if (!done) {
-        if (a == 0xFFFFFFFFu) {
-          done = true;
-        } else {
-          const int sz = aggsize[a];
-          if (better(c, sz, (int32_t)a, bc, bs, best)) {
-            best = (int32_t)a;
-            bc = c;
-            bs = sz;
-          }
-          last = (int32_t)a;
+    for (int j = 0; j < len; j++) {
+      const int32_t a = myw[j];
+      if (a < 0) continue;
+      int c = 0, first = j;
+      for (int k = 0; k < len; k++) {
+        if (myw[k] == a) {
+          c++;
+          first = min(first, k);
         }
       }
+      if (first != j) continue;  // counted at its first occurrence
+      const int sz = aggsize[a];
+      if (better(c, sz, a, bc, bs, best)) {
+        best = a;
+        bc = c;
+        bs = sz;
+      }
     }
-    if (active && lg == 0) {
-      labels[v] = best;
-      if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
-    }
+    labels[v] = best;
+    if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
   }
 }
 
-// Phase 3 for leftovers of degree >= block_degree: count coupling in
+// Phase 3, one block per medium leftover row: sort its neighbours'
+// tentative labels in shared memory, count each run, reduce the best run.
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_phase3_sort(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
+                                                        const int32_t* list, const int32_t* list_cnt, int32_t* labels,
+                                                        int32_t* err) {
+  __shared__ int32_t buf[kPhase3SortCap];
+  __shared__ uint32_t sh[40];
+  __shared__ int fill;
+  const int64_t n_items = *list_cnt;
+  for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int32_t v = list[it];
+    int64_t s, e;
+    row_range(g, v, s, e);
+    if (threadIdx.x == 0) fill = 0;
+    __syncthreads();
+    visit_row<kBlock>(g.colind, g.nnz, s, e, threadIdx.x, g.vec, [&](int32_t w) {
+      const int32_t t = w != v ? tent[w] : -1;
+      if (t >= 0) buf[atomicAdd(&fill, 1)] = t;
+    });
+    __syncthreads();
+    const int cnt = fill;
+    int P = 1;
+    while (P < cnt) P <<= 1;
+    for (int i = cnt + threadIdx.x; i < P; i += blockDim.x) buf[i] = 0x7FFFFFFF;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const int32_t x = buf[i], y = buf[ixj];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              buf[i] = y;
+              buf[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // each run start counts its run; best by (max count, min size, min id)
+    int lc = 0, ls = 0;
+    int32_t la = -1;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      if (i > 0 && buf[i - 1] == buf[i]) continue;
+      const int32_t a = buf[i];
+      int lo = i + 1, hi = cnt;  // first index past the run
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (buf[mid] == a) lo = mid + 1;
+        else hi = mid;
+      }
+      const int c = lo - i, sz = aggsize[a];
+      if (better(c, sz, a, lc, ls, la)) {
+        la = a;
+        lc = c;
+        ls = sz;
+      }
+    }
+    const uint32_t mc = block_max_u32(la >= 0 ? (uint32_t)lc : 0u, sh);
+    const uint32_t ms = block_min_u32(la >= 0 && (uint32_t)lc == mc ? (uint32_t)ls : 0xFFFFFFFFu, sh);
+    const uint32_t ma =
+        block_min_u32(la >= 0 && (uint32_t)lc == mc && (uint32_t)ls == ms ? (uint32_t)la : 0xFFFFFFFFu, sh);
+    if (threadIdx.x == 0) {
+      const int32_t best = mc > 0 ? (int32_t)ma : -1;
+      labels[v] = best;
+      if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
+    }
+    __syncthreads();
+  }
+}
+
+// Phase 3 for leftovers of degree > kPhase3SortCap: count coupling in
 // shared-memory windows of kPhase3Window aggregate ids.
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_block(GraphView<I> g, const int32_t* tent,
@@ -272,95 +359,118 @@ static void launch_claim(mis2_ctx* c, const GraphView<I>& gv, const int32_t* lis
 }
 
 template <typename I>
-static void launch_phase3(mis2_ctx* c, const GraphView<I>& gv, int G, int32_t* labels, cudaStream_t st) {
+static void launch_phase3(mis2_ctx* c, const GraphView<I>& gv, int32_t* labels, cudaStream_t st) {
   Scratch& s = c->s;
-  const int blocks = grid_for(c, gv.n, kBlock, 8);
-#define MIS2_P3(GG)                                                                                   \
-  k_phase3<GG, I><<<blocks, kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left, s.ctr + kCtrLeft, labels, \
-                                             s.ctr + kCtrErr)
-  switch (G) {
-    case 1: MIS2_P3(1); break;
-    case 2: MIS2_P3(2); break;
-    case 4: MIS2_P3(4); break;
-    case 8: MIS2_P3(8); break;
-    case 16: MIS2_P3(16); break;
-    default: MIS2_P3(32); break;
-  }
-#undef MIS2_P3
+  k_phase3_lane<I><<<grid_for(c, gv.n, kBlock, 8), kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left, s.ctr + kCtrLeft,
+                                                                     labels, s.ctr + kCtrErr);
+  k_phase3_sort<I><<<c->sm_count * 4, kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left_mid, s.ctr + kCtrLeftMid,
+                                                       labels, s.ctr + kCtrErr);
   k_phase3_block<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left_heavy,
                                                         s.ctr + kCtrLeftHeavy, labels, s.ctr + kCtrErr);
-  c->launches += 2;
+  c->launches += 3;
 }
 
 template <typename I>
-static int aggregate_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,
-                       int mode, int32_t* labels, int64_t* n_aggs, cudaStream_t st) {
+static int phase1_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, int32_t* labels,
+                    cudaStream_t st) {
   Scratch& s = c->s;
   const GraphView<I> gv = gview<I>(g);
-  const int64_t n = g.n;
-  c->stats.rounds2 = 0;
-  memset(c->stats.trace2, 0, sizeof(c->stats.trace2));
-  if (n == 0) {
-    *n_aggs = 0;
-    return MIS2_OK;
-  }
-  MIS2_CUDA(cudaMemsetAsync(labels, 0xFF, n * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(labels, 0xFF, g.n * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrM2, 0, (kCtrErr - kCtrM2 + 1) * sizeof(int32_t), st));
-  // phase 1
   timer_begin(c, kKcAggregate, st);
   launch_claim<I>(c, gv, roots, n_roots, nullptr, labels, 0, st);
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
-  int64_t nq = 0;
-  if (mode == MIS2_AGG_ALG3) {
-    // phase 2: MIS-2 of G minus the aggregated vertices
-    const PrioCfg p = make_prio(c, n, seed);
-    int32_t r2 = 0;
-    if (c->cfg.loop == MIS2_LOOP_DEVICE)
-      MIS2_TRY(mis2_rounds_device(c, g, labels, p, 1, st, &r2));
-    else
-      MIS2_TRY(mis2_rounds_host(c, g, labels, p, 1, st, &r2));
-    c->stats.rounds2 = r2;
-    MIS2_TRY(extract_in_set(c, n, nullptr, s.roots2, s.ctr + kCtrM2, st));
-    MIS2_CUDA(cudaMemsetAsync(s.qflag, 0, n, st));
-    timer_begin(c, kKcAggregate, st);
-    k_qualify<I><<<grid_for(c, n, kBlock / 32), kBlock, 0, st>>>(gv, s.roots2, s.ctr + kCtrM2, labels, s.qflag);
-    c->launches++;
-    timer_end(c, st);
-    MIS2_CUDA(cudaGetLastError());
-    MIS2_TRY(compact_flags(c, s.qflag, nullptr, n, s.qlist, s.ctr + kCtrQual, st));
-    timer_begin(c, kKcAggregate, st);
-    launch_claim<I>(c, gv, s.qlist, 0, s.ctr + kCtrQual, labels, (int32_t)n_roots, st);
-    timer_end(c, st);
-    MIS2_CUDA(cudaGetLastError());
-    MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    MIS2_CUDA(cudaStreamSynchronize(st));
-    nq = c->h_ctr[kCtrQual];
-  }
-  const int64_t total = n_roots + nq;
-  // phase 3: leftovers join by coupling, read from the frozen labels
+  return MIS2_OK;
+}
+
+// Phase 2 leaves the qualifying phase-2 roots, ascending, in s.qlist.
+template <typename I>
+static int phase2_t(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* labels, int32_t label_base,
+                    int32_t* rounds2, int64_t* nq, cudaStream_t st) {
+  Scratch& s = c->s;
+  const GraphView<I> gv = gview<I>(g);
+  const int64_t n = g.n;
+  if (c->cfg.loop == MIS2_LOOP_DEVICE)
+    MIS2_TRY(mis2_rounds_device(c, g, labels, p, 1, st, rounds2));
+  else
+    MIS2_TRY(mis2_rounds_host(c, g, labels, p, 1, st, rounds2));
+  MIS2_TRY(extract_in_set(c, n, nullptr, s.roots2, s.ctr + kCtrM2, st));
+  MIS2_CUDA(cudaMemsetAsync(s.qflag, 0, n, st));
+  timer_begin(c, kKcAggregate, st);
+  k_qualify<I><<<grid_for(c, n, kBlock / 32), kBlock, 0, st>>>(gv, s.roots2, s.ctr + kCtrM2, labels, s.qflag);
+  c->launches++;
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  MIS2_TRY(compact_flags(c, s.qflag, nullptr, n, s.qlist, s.ctr + kCtrQual, st));
+  timer_begin(c, kKcAggregate, st);
+  launch_claim<I>(c, gv, s.qlist, 0, s.ctr + kCtrQual, labels, label_base, st);
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MIS2_CUDA(cudaStreamSynchronize(st));
+  *nq = c->h_ctr[kCtrQual];
+  return MIS2_OK;
+}
+
+template <typename I>
+static int phase3_t(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, cudaStream_t st) {
+  Scratch& s = c->s;
+  const GraphView<I> gv = gview<I>(g);
+  const int64_t n = g.n;
   timer_begin(c, kKcAggregate, st);
   MIS2_CUDA(cudaMemcpyAsync(s.tent, labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   MIS2_CUDA(cudaMemsetAsync(s.aggsize, 0, std::max<int64_t>(total, 1) * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeft, 0, 2 * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrErr, 0, sizeof(int32_t), st));
   k_aggsize<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, s.tent, s.aggsize);
-  k_leftovers<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.left, s.ctr + kCtrLeft, s.left_heavy,
-                                                             s.ctr + kCtrLeftHeavy, c->cfg.block_degree);
+  k_leftovers<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.left, s.ctr + kCtrLeft, s.left_mid,
+                                                             s.ctr + kCtrLeftMid, s.left_heavy, s.ctr + kCtrLeftHeavy);
   c->launches += 2;
-  launch_phase3<I>(c, gv, pick_group_lanes(c, g), labels, st);
+  launch_phase3<I>(c, gv, labels, st);
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MIS2_CUDA(cudaStreamSynchronize(st));
   if (c->h_ctr[kCtrErr] & kErrNoAggregatedNeighbour) return MIS2_ERR_BAD_GRAPH;
-  *n_aggs = total;
   return MIS2_OK;
+}
+
+int agg_phase1(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, int32_t* labels,
+               cudaStream_t st) {
+  return g.rp64 ? phase1_t<int64_t>(c, g, roots, n_roots, labels, st)
+                : phase1_t<int32_t>(c, g, roots, n_roots, labels, st);
+}
+
+int agg_phase2(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* labels, int32_t label_base,
+               int32_t* rounds2, int64_t* nq, cudaStream_t st) {
+  return g.rp64 ? phase2_t<int64_t>(c, g, p, labels, label_base, rounds2, nq, st)
+                : phase2_t<int32_t>(c, g, p, labels, label_base, rounds2, nq, st);
+}
+
+int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, cudaStream_t st) {
+  return g.rp64 ? phase3_t<int64_t>(c, g, labels, total, st) : phase3_t<int32_t>(c, g, labels, total, st);
 }
 
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed, int mode,
                    int32_t* labels, int64_t* n_aggs, cudaStream_t st) {
-  return g.rp64 ? aggregate_t<int64_t>(c, g, roots, n_roots, seed, mode, labels, n_aggs, st)
-                : aggregate_t<int32_t>(c, g, roots, n_roots, seed, mode, labels, n_aggs, st);
+  c->stats.rounds2 = 0;
+  memset(c->stats.trace2, 0, sizeof(c->stats.trace2));
+  if (g.n == 0) {
+    *n_aggs = 0;
+    return MIS2_OK;
+  }
+  MIS2_TRY(agg_phase1(c, g, roots, n_roots, labels, st));
+  int64_t nq = 0;
+  if (mode == MIS2_AGG_ALG3) {
+    int32_t r2 = 0;
+    MIS2_TRY(agg_phase2(c, g, make_prio(c, g.n, seed), labels, (int32_t)n_roots, &r2, &nq, st));
+    c->stats.rounds2 = r2;
+  }
+  MIS2_TRY(agg_phase3(c, g, labels, n_roots + nq, st));
+  *n_aggs = n_roots + nq;
+  return MIS2_OK;
 }
 
 }  // namespace mis2

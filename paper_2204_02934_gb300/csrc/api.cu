@@ -68,6 +68,9 @@ PrioCfg make_prio(const mis2_ctx* c, int64_t n, uint64_t seed) {
   p.table = nullptr;
   p.table_n = n;
   p.table_rounds = 0;
+  p.gid = nullptr;
+  p.voff = nullptr;
+  p.gbits = nullptr;
   p.b = id_bits(n);
   p.variant = c->cfg.hash_variant;
   p.pad = 0;
@@ -82,7 +85,7 @@ static int validate_cfg(const mis2_config* cfg) {
   if (cfg->warp_degree < 1 || cfg->block_degree < cfg->warp_degree) return MIS2_ERR_INVALID_ARG;
   if (cfg->block_size != kBlock) return MIS2_ERR_INVALID_ARG;
   if (cfg->loop != MIS2_LOOP_HOST && cfg->loop != MIS2_LOOP_DEVICE) return MIS2_ERR_INVALID_ARG;
-  if (cfg->spin_limit < 1) return MIS2_ERR_INVALID_ARG;
+  if (cfg->spin_limit < 1 || cfg->loop_blocks_per_sm < 0) return MIS2_ERR_INVALID_ARG;
   return MIS2_OK;
 }
 
@@ -149,6 +152,7 @@ static int alloc_scratch(mis2_ctx* c) {
   MIS2_TRY(dev_alloc(c, &s.aggsize, n));
   MIS2_TRY(dev_alloc(c, &s.left, n));
   MIS2_TRY(dev_alloc(c, &s.left_heavy, n));
+  MIS2_TRY(dev_alloc(c, &s.left_mid, n));
   MIS2_TRY(dev_alloc(c, &s.roots_tmp, n));
   MIS2_TRY(dev_alloc(c, &s.agg_cnt, n + 1));
   MIS2_TRY(dev_alloc(c, &s.agg_ptr, n + 1));
@@ -157,11 +161,10 @@ static int alloc_scratch(mis2_ctx* c) {
   MIS2_TRY(dev_alloc(c, &s.cursor, n + 1));
   MIS2_TRY(dev_alloc(c, &s.members, n));
   MIS2_TRY(dev_alloc(c, &s.c_cnt, n + 1));
-  MIS2_TRY(dev_alloc(c, &s.lo, n));
-  MIS2_TRY(dev_alloc(c, &s.hi, n));
   MIS2_TRY(dev_alloc(c, &s.large, n));
   MIS2_TRY(dev_alloc(c, &s.tmp, nnz + 4));
   MIS2_TRY(dev_alloc(c, &s.labels_tmp, n));
+  MIS2_TRY(dev_alloc(c, &s.bitmaps, (int64_t)coarse_bitmap_blocks(c) * ((n + 31) / 32)));
   if (cudaMallocHost(&c->h_ctr, kCtrWords * sizeof(int32_t)) != cudaSuccess) return MIS2_ERR_OUT_OF_MEMORY;
   if (cudaMallocHost(&c->h_trace, 2 * MIS2_TRACE_CAP * 4 * sizeof(int64_t)) != cudaSuccess)
     return MIS2_ERR_OUT_OF_MEMORY;
@@ -220,7 +223,7 @@ void mis2_config_default(mis2_config* cfg) {
   cfg->hash_variant = MIS2_HASH_XORSHIFT_STAR;
   cfg->agg_mode = MIS2_AGG_ALG3;
   cfg->group_lanes = 0;
-  cfg->warp_degree = 64;
+  cfg->warp_degree = 32;
   cfg->block_degree = 2048;
   cfg->block_size = kBlock;
   cfg->loop = MIS2_LOOP_HOST;

@@ -3,23 +3,34 @@
 // fine edge joins a member of A to a member of B, A != B).
 //
 // No global sort: vertices are bucketed by aggregate (counting sort), then
-// each aggregate's neighbour labels are de-duplicated on chip:
-//   - narrow label range (<= 4096 ids): a per-warp bitmap, read out in order;
-//   - few entries (<= 1024): a per-warp bitonic sort in shared memory;
-//   - otherwise: a block walks the label range in 32768-bit windows.
+// each aggregate's neighbour labels are de-duplicated on chip.
+//   - Aggregates whose members hold <= kWarpEntries entries: one warp.  A
+//     first walk finds the label range and count; a narrow range (<= 4096
+//     ids) goes through a shared-memory bitmap read out in order, few
+//     entries (<= 1024) through a shared-memory bitonic sort.
+//   - Everything else: one block with a global bitmap over all aggregate
+//     ids.  Each first-time bit flip appends the label to a discovery list;
+//     the list (the coarse row, unordered) is sorted in shared memory when it
+//     fits, otherwise the bitmap is read out in order.  Bits are cleared
+//     again, so the bitmap stays zero between aggregates.
+// Member rows of <= 32 entries are staged lane-per-row with asynchronous
+// copies; longer rows are walked by the whole warp.
 // Rows land in a scratch buffer at the aggregate's degree-sum offset, then
 // are packed behind the prefix sum of the row lengths.
 #include <algorithm>
 
 #include "internal.h"
+#include "mis_rows.cuh"
 #include "scan.cuh"
 
 namespace mis2 {
 
-constexpr int kBitmapWords = 128;    // 4096 ids per warp
-constexpr int kSortCap = 1024;       // entries per warp
-constexpr int kWarpsPerBlock = kBlock / 32;
-constexpr int kLargeWords = 1024;    // 32768 ids per block window
+constexpr int kCoarseWarps = 4;        // warps per block of the warp-per-aggregate kernel
+constexpr int kBitmapWords = 128;      // 4096 ids per warp
+constexpr int kSortCap = 1024;         // entries per warp
+constexpr int kWarpEntries = 8192;     // larger aggregates go to the block kernel
+constexpr int kBlockSortCap = 8192;    // discovery lists sorted in shared memory up to this size
+static_assert(kBlockSortCap * 4 <= (kBlock / 32) * kStageWarpInt4 * 16, "sort buffer reuses the staging area");
 
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_hist(GraphView<I> g, const int32_t* labels, int32_t* agg_cnt,
@@ -55,20 +66,40 @@ __global__ void __launch_bounds__(kBlock) k_coarse_scatter(int64_t n, const int3
   }
 }
 
-// Walk every fine entry of aggregate a's members with G lanes per member
-// row; f(label) is called for neighbour labels != a.  Warp-uniform.
-template <int G, typename I, typename F>
+// Walk every fine entry of aggregate a (members [mb, me)) with one warp and
+// call f(label) for each neighbour label != a.  Warp-uniform; f runs in the
+// lane that holds the entry.
+template <typename I, typename F>
 __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int32_t* labels, const int32_t* members,
-                                               int64_t mb, int64_t me, int32_t a, F&& f) {
-  constexpr int RPW = 32 / G;
-  const int lane = lane_id(), lg = lane & (G - 1), sub = lane / G;
-  for (int64_t kb = mb; kb < me; kb += RPW) {
-    const int64_t k = kb + sub;
-    if (k < me) {
-      const int32_t u = members[k];
-      int64_t s, e;
-      row_range(g, u, s, e);
-      visit_row<G>(g.colind, g.nnz, s, e, lg, g.vec, [&](int32_t w) {
+                                               int64_t mb, int64_t me, int32_t a, int4* stage_warp, F&& f) {
+  const int lane = lane_id();
+  int4* my = stage_warp + lane * kStageInt4;
+  const int32_t* myw = reinterpret_cast<const int32_t*>(my);
+  for (int64_t kb = mb; kb < me; kb += 32) {
+    const int64_t k = kb + lane;
+    int64_t s = 0, e = 0;
+    int off = -1;
+    const bool has = k < me;
+    if (has) {
+      row_range(g, members[k], s, e);
+      off = stage_row(g, s, e, my);
+    }
+    cp_async_wait_all();
+    if (off >= 0) {
+      const int len = (int)(e - s);
+      int32_t lab[kLaneRowMax];
+#pragma unroll
+      for (int j = 0; j < kLaneRowMax; j++) lab[j] = j < len ? labels[myw[off + j]] : a;
+#pragma unroll
+      for (int j = 0; j < kLaneRowMax; j++)
+        if (lab[j] != a) f(lab[j]);
+    }
+    unsigned longm = __ballot_sync(kFull, has && off < 0);
+    while (longm) {
+      const int j = __ffs(longm) - 1;
+      longm &= longm - 1;
+      const int64_t sj = __shfl_sync(kFull, s, j), ej = __shfl_sync(kFull, e, j);
+      visit_row<32>(g.colind, g.nnz, sj, ej, lane, g.vec, [&](int32_t w) {
         const int32_t l = labels[w];
         if (l != a) f(l);
       });
@@ -76,22 +107,25 @@ __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int3
   }
 }
 
-template <int G, typename I>
-__global__ void __launch_bounds__(kBlock) k_coarse_rows(GraphView<I> g, const int32_t* labels, int64_t n_aggs,
-                                                        const int32_t* agg_ptr, const int32_t* members,
-                                                        const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt,
-                                                        int32_t* lo_arr, int32_t* hi_arr, int32_t* large,
-                                                        int32_t* large_cnt) {
-  __shared__ int32_t sbuf[kWarpsPerBlock][kSortCap];
-  __shared__ int32_t scnt[kWarpsPerBlock];
+template <typename I>
+__global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
+    GraphView<I> g, const int32_t* labels, int64_t n_aggs, const int32_t* agg_ptr, const int32_t* members,
+    const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt, int32_t* large, int32_t* large_cnt) {
+  __shared__ int32_t sbuf[kCoarseWarps][kSortCap];
+  __shared__ int4 stage[kCoarseWarps][kStageWarpInt4];
+  __shared__ int32_t scnt[kCoarseWarps];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
   int32_t* buf = sbuf[wib];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
+    if (ub[a] > kWarpEntries) {
+      if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
+      continue;
+    }
     const int64_t mb = agg_ptr[a], me = agg_ptr[a + 1];
     uint32_t lo = 0xFFFFFFFFu, hi = 0u;
     int cnt = 0;
-    walk_aggregate<G, I>(g, labels, members, mb, me, (int32_t)a, [&](int32_t l) {
+    walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](int32_t l) {
       lo = min(lo, (uint32_t)l);
       hi = max(hi, (uint32_t)l);
       cnt++;
@@ -108,7 +142,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rows(GraphView<I> g, const in
       uint32_t* bm = reinterpret_cast<uint32_t*>(buf);
       for (int j = lane; j < kBitmapWords; j += 32) bm[j] = 0u;
       __syncwarp();
-      walk_aggregate<G, I>(g, labels, members, mb, me, (int32_t)a, [&](int32_t l) {
+      walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](int32_t l) {
         const uint32_t d = (uint32_t)l - lo;
         atomicOr(bm + (d >> 5), 1u << (d & 31));
       });
@@ -145,9 +179,8 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rows(GraphView<I> g, const in
     if (cnt <= kSortCap) {
       if (lane == 0) scnt[wib] = 0;
       __syncwarp();
-      walk_aggregate<G, I>(g, labels, members, mb, me, (int32_t)a, [&](int32_t l) {
-        buf[atomicAdd(scnt + wib, 1)] = l;
-      });
+      walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib],
+                        [&](int32_t l) { buf[atomicAdd(scnt + wib, 1)] = l; });
       __syncwarp();
       int P = 32;
       while (P < cnt) P <<= 1;
@@ -181,70 +214,86 @@ __global__ void __launch_bounds__(kBlock) k_coarse_rows(GraphView<I> g, const in
       __syncwarp();
       continue;
     }
-    if (lane == 0) {
-      lo_arr[a] = (int32_t)lo;
-      hi_arr[a] = (int32_t)hi;
-      large[atomicAdd(large_cnt, 1)] = (int32_t)a;
-    }
+    if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
   }
 }
 
+// Block per large aggregate; `bitmaps` holds one zeroed bitmap of `words`
+// words per block.
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_large(GraphView<I> g, const int32_t* labels,
                                                          const int32_t* agg_ptr, const int32_t* members,
-                                                         const int32_t* ub_ptr, const int32_t* lo_arr,
-                                                         const int32_t* hi_arr, const int32_t* large,
-                                                         const int32_t* large_cnt, int32_t* tmp, int32_t* c_cnt) {
-  __shared__ uint32_t bm[kLargeWords];
+                                                         const int32_t* ub_ptr, const int32_t* large,
+                                                         const int32_t* large_cnt, uint32_t* bitmaps, int64_t words,
+                                                         int32_t* tmp, int32_t* c_cnt) {
+  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  int32_t* sorted = reinterpret_cast<int32_t*>(&stage[0][0]);  // reused once the walk is done
+  __shared__ int disc;
   __shared__ int sh[40];
+  uint32_t* bm = bitmaps + (int64_t)blockIdx.x * words;
   const int64_t nl = *large_cnt;
-  constexpr int WPT = kLargeWords / kBlock;  // words per thread
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
   for (int64_t li = blockIdx.x; li < nl; li += gridDim.x) {
     const int32_t a = large[li];
     const int64_t mb = agg_ptr[a], me = agg_ptr[a + 1];
-    const int64_t lo = lo_arr[a], hi = hi_arr[a];
     const int64_t out = ub_ptr[a];
-    int64_t run = 0;
-    for (int64_t wb = lo; wb <= hi; wb += 32 * kLargeWords) {
-      for (int j = threadIdx.x; j < kLargeWords; j += blockDim.x) bm[j] = 0u;
+    if (threadIdx.x == 0) disc = 0;
+    __syncthreads();
+    // each warp walks a contiguous share of the members
+    const int64_t per = (me - mb + (kBlock / 32) - 1) / (kBlock / 32);
+    const int64_t w0 = mb + wib * per, w1 = min(me, w0 + per);
+    walk_aggregate<I>(g, labels, members, w0, max(w0, w1), a, stage[wib], [&](int32_t l) {
+      const uint32_t bit = 1u << (l & 31);
+      const uint32_t old = atomicOr(bm + (l >> 5), bit);
+      if ((old & bit) == 0u) tmp[out + atomicAdd(&disc, 1)] = l;
+    });
+    __syncthreads();
+    const int D = disc;
+    if (D <= kBlockSortCap) {
+      int P = 1;
+      while (P < D) P <<= 1;
+      for (int i = threadIdx.x; i < P; i += blockDim.x) sorted[i] = i < D ? tmp[out + i] : 0x7FFFFFFF;
       __syncthreads();
-      // each warp takes every 8th member row
-      const int lane = lane_id(), wib = threadIdx.x >> 5;
-      for (int64_t k = mb + wib; k < me; k += kWarpsPerBlock) {
-        const int32_t u = members[k];
-        int64_t s, e;
-        row_range(g, u, s, e);
-        visit_row<32>(g.colind, g.nnz, s, e, lane, g.vec, [&](int32_t w) {
-          const int32_t l = labels[w];
-          if (l != a && l >= wb && l < wb + 32 * kLargeWords) {
-            const int64_t d = l - wb;
-            atomicOr(bm + (d >> 5), 1u << (d & 31));
+      for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            const int ixj = i ^ j;
+            if (ixj > i) {
+              const int32_t x = sorted[i], y = sorted[ixj];
+              const bool up = (i & k) == 0;
+              if ((x > y) == up) {
+                sorted[i] = y;
+                sorted[ixj] = x;
+              }
+            }
           }
-        });
+          __syncthreads();
+        }
       }
-      __syncthreads();
-      uint32_t wv[WPT];
-      int pc = 0;
-#pragma unroll
-      for (int q = 0; q < WPT; q++) {
-        wv[q] = bm[threadIdx.x * WPT + q];
-        pc += __popc(wv[q]);
+      for (int i = threadIdx.x; i < D; i += blockDim.x) {
+        const int32_t l = sorted[i];
+        tmp[out + i] = l;
+        bm[l >> 5] = 0u;  // clear for the next aggregate (idempotent per word)
       }
-      int total;
-      int pos = block_exclusive_scan(pc, sh, &total);
-#pragma unroll
-      for (int q = 0; q < WPT; q++) {
-        uint32_t w = wv[q];
+    } else {
+      // read the whole bitmap out in order, clearing it
+      int64_t run = 0;
+      for (int64_t wb = 0; wb < words; wb += blockDim.x) {
+        const int64_t wi = wb + threadIdx.x;
+        uint32_t w = wi < words ? bm[wi] : 0u;
+        int total;
+        int pos = block_exclusive_scan(__popc(w), sh, &total);
+        if (w != 0u) bm[wi] = 0u;
         while (w) {
           const int bit = __ffs(w) - 1;
           w &= w - 1;
-          tmp[out + run + pos++] = (int32_t)(wb + (int64_t)(threadIdx.x * WPT + q) * 32 + bit);
+          tmp[out + run + pos++] = (int32_t)(wi * 32 + bit);
         }
+        run += total;
       }
-      run += total;
-      __syncthreads();
     }
-    if (threadIdx.x == 0) c_cnt[a] = (int32_t)run;
+    if (threadIdx.x == 0) c_cnt[a] = D;
+    __syncthreads();
   }
 }
 
@@ -261,6 +310,12 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const in
 }
 
 // ------------------------------------------------------------------ host side
+int coarse_bitmap_blocks(const mis2_ctx* c) {
+  const int64_t words = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
+  const int64_t cap = ((int64_t)256 << 20) / (words * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sm_count * 2, cap));
+}
+
 template <typename I>
 static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                      int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st) {
@@ -290,22 +345,14 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   timer_begin(c, kKcCoarse, st);
   MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   k_coarse_scatter<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, labels, s.cursor, s.members);
-  const int G = pick_group_lanes(c, g);
-  const int blocks = grid_for(c, n_aggs, kWarpsPerBlock, 8);
-#define MIS2_CR(GG)                                                                                           \
-  k_coarse_rows<GG, I><<<blocks, kBlock, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub_ptr, s.tmp, \
-                                                  s.c_cnt, s.lo, s.hi, s.large, s.ctr + kCtrLarge)
-  switch (G) {
-    case 1: MIS2_CR(1); break;
-    case 2: MIS2_CR(2); break;
-    case 4: MIS2_CR(4); break;
-    case 8: MIS2_CR(8); break;
-    case 16: MIS2_CR(16); break;
-    default: MIS2_CR(32); break;
-  }
-#undef MIS2_CR
-  k_coarse_large<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.ub_ptr, s.lo, s.hi,
-                                                         s.large, s.ctr + kCtrLarge, s.tmp, s.c_cnt);
+  const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
+  k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge);
+  const int64_t words = (n_aggs + 31) / 32;
+  const int nb = coarse_bitmap_blocks(c);
+  MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)nb * words * sizeof(uint32_t), st));
+  k_coarse_large<I><<<nb, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.ub_ptr, s.large, s.ctr + kCtrLarge,
+                                           s.bitmaps, words, s.tmp, s.c_cnt);
   c->launches += 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
@@ -315,8 +362,8 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   const int64_t total = c->h_ctr[kCtrCnnz];
   if (total > c_colind_cap) return MIS2_ERR_INVALID_ARG;
   timer_begin(c, kKcCoarse, st);
-  k_coarse_pack<<<grid_for(c, n_aggs, kWarpsPerBlock, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr,
-                                                                            s.tmp, c_colind);
+  k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
+                                                                        c_colind);
   c->launches++;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());

@@ -35,11 +35,17 @@ __host__ __device__ __forceinline__ uint64_t xorshift64(uint64_t x) {
   return x;
 }
 
-// Everything a kernel needs to build T_v for a round.
+// Everything a kernel needs to build T_v for a round.  For a batch of
+// graphs stored as one block-diagonal union, gid maps a union vertex to its
+// graph, whose own id bits and first union vertex give the tuple that graph
+// would get on its own (tuples are only ever compared inside one graph).
 struct PrioCfg {
   uint64_t seed;
   const uint32_t* table;  // test hook (Fig. 1): per-round priorities, or null
   int64_t table_n;        // row length of the table
+  const int32_t* gid;     // batch: graph of each union vertex, or null
+  const int64_t* voff;    // batch: first union vertex of each graph
+  const int32_t* gbits;   // batch: id bits of each graph
   int32_t table_rounds;
   int32_t b;              // id bits, b = ceil(log2(n + 2))
   int32_t variant;        // MIS2_HASH_*
@@ -50,6 +56,12 @@ struct PrioCfg {
 // as priority.  2^b >= n + 2 keeps the result away from IN (0) and OUT.
 __device__ __forceinline__ uint32_t make_tuple(const PrioCfg& p, uint32_t iter, uint32_t v) {
   uint32_t prio;
+  int b = p.b;
+  if (p.gid != nullptr) {
+    const int32_t g = p.gid[v];
+    v -= (uint32_t)p.voff[g];
+    b = p.gbits[g];
+  }
   if (p.table != nullptr && (int32_t)iter < p.table_rounds) {
     prio = p.table[(int64_t)iter * p.table_n + v];
   } else {
@@ -60,9 +72,9 @@ __device__ __forceinline__ uint32_t make_tuple(const PrioCfg& p, uint32_t iter, 
       const uint64_t it = p.variant == MIS2_HASH_FIXED ? 0ull : (uint64_t)iter;
       h = xorshift_star64(xorshift_star64(it) ^ xorshift_star64((uint64_t)v) ^ p.seed);
     }
-    prio = p.b >= 32 ? 0u : (uint32_t)(h >> (32 + p.b));
+    prio = b >= 32 ? 0u : (uint32_t)(h >> (32 + b));
   }
-  return (p.b >= 32 ? 0u : (prio << p.b)) | (v + 1u);
+  return (b >= 32 ? 0u : (prio << b)) | (v + 1u);
 }
 
 __host__ __device__ inline int id_bits(int64_t n) {
@@ -120,6 +132,16 @@ __device__ __forceinline__ void visit_row(const int32_t* __restrict__ colind, in
   } else {
     for (int64_t p = s + lg; p < e; p += G) f(__ldg(colind + p));
   }
+}
+
+// 16-byte global -> shared copies that bypass L1 (LDGSTS); each thread waits
+// for its own copies only.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ----------------------------------------------------------------- reductions

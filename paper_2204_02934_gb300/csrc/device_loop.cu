@@ -75,6 +75,8 @@ struct LoopArgs {
 template <int G, typename I>
 __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
   __shared__ uint32_t sh[40];
+  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  int4* my_stage = stage[threadIdx.x >> 5];
   int32_t* ctr = a.ctr;
   int32_t* bar_count = ctr + kCtrBarrier;
   int32_t* bar_gen = ctr + kCtrBarrier + 1;
@@ -112,8 +114,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg 
     // ---- column step
     if (tid < kClasses) ctr[ctr_c1(nslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 1] = w2;
-    column_group_rows<G, I, false>(g, a.T, a.M, in2.l[0], n2[0], out2.l[0], ctr + ctr_c2(nslot, 0), d2, warp,
-                                   nwarps);
+    if constexpr (G == 1)
+      column_lane_rows<I, false>(g, a.T, a.M, in2.l[0], n2[0], out2.l[0], ctr + ctr_c2(nslot, 0), d2, warp, nwarps,
+                                 my_stage);
+    else
+      column_group_rows<G, I, false>(g, a.T, a.M, in2.l[0], n2[0], out2.l[0], ctr + ctr_c2(nslot, 0), d2, warp,
+                                     nwarps);
     if (n2[1] > 0)
       column_group_rows<32, I, false>(g, a.T, a.M, in2.l[1], n2[1], out2.l[1], ctr + ctr_c2(nslot, 1), d2, warp,
                                       nwarps);
@@ -124,8 +130,12 @@ __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg 
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = w1;
-    decide_group_rows<G, I, false>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
-                                   (uint32_t)(r + 1), warp, nwarps);
+    if constexpr (G == 1)
+      decide_lane_rows<I, false>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
+                                 (uint32_t)(r + 1), warp, nwarps, my_stage);
+    else
+      decide_group_rows<G, I, false>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
+                                     (uint32_t)(r + 1), warp, nwarps);
     if (n1[1] > 0)
       decide_group_rows<32, I, false>(g, a.T, a.M, in1.l[1], n1[1], out1.l[1], ctr + ctr_c1(nslot, 1), d1, p,
                                       (uint32_t)(r + 1), warp, nwarps);
@@ -143,7 +153,8 @@ static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cud
   int per_sm = 0;
   MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MIS2_ERR_CUDA;
-  const int blocks = c->sm_count * std::min(per_sm, 4);
+  const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 4;
+  const int blocks = c->sm_count * std::min(per_sm, want);
   c->device_loop_blocks = blocks;
   void* args[] = {&gv, &p, &la};
   MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));

@@ -29,6 +29,7 @@ enum : int {
   kCtrErr = 26,      // device error flags (bit 0: barrier timeout)
   kCtrRounds = 27,   // rounds of the device loop
   kCtrBarrier = 28,  // grid barrier: arrive count (28), generation (29)
+  kCtrLeftMid = 30,  // phase-3 leftovers of medium degree
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 32;
@@ -59,6 +60,7 @@ struct Scratch {
   int32_t* aggsize = nullptr;
   int32_t* left = nullptr;
   int32_t* left_heavy = nullptr;
+  int32_t* left_mid = nullptr;
   int32_t* roots_tmp = nullptr;  // root list when the caller passes none
   int32_t* agg_cnt = nullptr;
   int32_t* agg_ptr = nullptr;
@@ -67,10 +69,9 @@ struct Scratch {
   int32_t* cursor = nullptr;
   int32_t* members = nullptr;
   int32_t* c_cnt = nullptr;
-  int32_t* lo = nullptr;
-  int32_t* hi = nullptr;
   int32_t* large = nullptr;
   int32_t* tmp = nullptr;        // coarse rows before packing (max_nnz)
+  uint32_t* bitmaps = nullptr;   // coarse graph: one bitmap over aggregate ids per large-row block
   int32_t* labels_tmp = nullptr; // labels when the caller passes none
 };
 
@@ -162,6 +163,12 @@ int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out
 int compact_flags(mis2_ctx* c, const uint8_t* flags, const int32_t* map, int64_t n, int32_t* out,
                   int32_t* count_dev, cudaStream_t st);
 
+// Aggregation phases (Algorithm 3), exposed for the batched engine.
+int agg_phase1(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, int32_t* labels,
+               cudaStream_t st);
+int agg_phase2(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* labels, int32_t label_base,
+               int32_t* rounds2, int64_t* nq, cudaStream_t st);
+int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, cudaStream_t st);
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,
                    int mode, int32_t* labels, int64_t* n_aggs, cudaStream_t st);
 int coarsen_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
@@ -170,5 +177,6 @@ int run_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, uint8_t* in_set,
              int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
 
 PrioCfg make_prio(const mis2_ctx* c, int64_t n, uint64_t seed);
+int coarse_bitmap_blocks(const mis2_ctx* c);
 
 }  // namespace mis2

@@ -55,6 +55,30 @@ __global__ void __launch_bounds__(kBlock) k_decide(GraphView<I> g, uint32_t* T, 
 }
 
 template <typename I>
+__global__ void __launch_bounds__(kBlock) k_column_lane(GraphView<I> g, const uint32_t* T, uint32_t* M,
+                                                        const int32_t* wl_in, const int32_t* cnt_in, int32_t* wl_out,
+                                                        int32_t* cnt_out, int32_t* zero, PhaseTrace tr) {
+  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  phase_prologue(zero, tr);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  column_lane_rows<I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, tr.d, warp, nw, stage[threadIdx.x >> 5]);
+}
+
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_decide_lane(GraphView<I> g, uint32_t* T, const uint32_t* M,
+                                                        const int32_t* wl_in, const int32_t* cnt_in, int32_t* wl_out,
+                                                        int32_t* cnt_out, int32_t* zero, PhaseTrace tr, PrioCfg p,
+                                                        uint32_t next_iter) {
+  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  phase_prologue(zero, tr);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  decide_lane_rows<I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, tr.d, p, next_iter, warp, nw,
+                            stage[threadIdx.x >> 5]);
+}
+
+template <typename I>
 __global__ void __launch_bounds__(kBlock) k_column_block(GraphView<I> g, const uint32_t* T, uint32_t* M,
                                                          const int32_t* wl_in, const int32_t* cnt_in,
                                                          int32_t* wl_out, int32_t* cnt_out, int64_t* dsum) {
@@ -148,11 +172,13 @@ int grid_for(const mis2_ctx* c, int64_t items, int items_per_block, int blocks_p
 int pick_group_lanes(const mis2_ctx* c, const GraphArgs& g) {
   if (c->cfg.group_lanes > 0) return c->cfg.group_lanes;
   const double avg = g.n > 0 ? (double)g.nnz / (double)g.n : 0.0;
-  if (avg < 6) return 1;
-  if (avg < 12) return 2;
-  if (avg < 24) return 4;
-  if (avg < 48) return 8;
-  if (avg < 96) return 16;
+  // A lane per row keeps 32 independent rows in flight per warp; wider
+  // groups only pay off once rows are long (heavier rows go to the warp and
+  // block classes anyway).
+  if (avg < 40) return 1;
+  if (avg < 80) return 2;
+  if (avg < 160) return 4;
+  if (avg < 320) return 8;
   return 32;
 }
 
@@ -181,7 +207,9 @@ static void launch_column(mis2_ctx* c, const GraphView<I>& gv, int G, int cls, i
 #define MIS2_COL(GG) \
   k_column<GG, I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, tr)
   switch (G) {
-    case 1: MIS2_COL(1); break;
+    case 1:
+      k_column_lane<I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, tr);
+      break;
     case 2: MIS2_COL(2); break;
     case 4: MIS2_COL(4); break;
     case 8: MIS2_COL(8); break;
@@ -206,7 +234,10 @@ static void launch_decide(mis2_ctx* c, const GraphView<I>& gv, int G, int cls, i
   k_decide<GG, I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, tr, \
                                              p, next_iter)
   switch (G) {
-    case 1: MIS2_DEC(1); break;
+    case 1:
+      k_decide_lane<I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, tr, p,
+                                                  next_iter);
+      break;
     case 2: MIS2_DEC(2); break;
     case 4: MIS2_DEC(4); break;
     case 8: MIS2_DEC(8); break;

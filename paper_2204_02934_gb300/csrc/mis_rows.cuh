@@ -26,6 +26,130 @@ struct RowLists {
   int32_t* l[kClasses];
 };
 
+// Lane-per-row rows (G = 1) stage their column indices in shared memory with
+// asynchronous 16-byte copies issued all at once, then issue every neighbour
+// gather back to back: a row costs about two memory latencies instead of one
+// per 16-byte chunk.
+constexpr int kLaneRowMax = 32;                          // entries staged per lane
+constexpr int kStageInt4 = (kLaneRowMax + 3) / 4 + 1;   // 9 int4 cover 32 entries at any alignment
+constexpr int kStageWarpInt4 = 32 * kStageInt4;
+
+// Stage colind[s, e) into `my`; returns the word offset of colind[s] inside
+// the staged words, or -1 when the row does not fit (too long, buffer not
+// 16-byte aligned, or the last 16-byte chunk would pass nnz).
+template <typename I>
+__device__ __forceinline__ int stage_row(const GraphView<I>& g, int64_t s, int64_t e, int4* my) {
+  if (!g.vec || e - s > kLaneRowMax) return -1;
+  const int64_t a = s & ~int64_t(3);
+  const int nq = (int)((e - a + 3) >> 2);
+  if (a + 4 * (int64_t)nq > g.nnz) return -1;
+#pragma unroll
+  for (int k = 0; k < kStageInt4; k++)
+    if (k < nq) cp_async16(my + k, g.colind + a + 4 * k);
+  return (int)(s - a);
+}
+
+template <typename I, bool NC>
+__device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const uint32_t* T, uint32_t* M,
+                                                 const int32_t* wl_in, int n_in, int32_t* wl_out, int32_t* cnt_out,
+                                                 int64_t* dsum, int64_t warp_begin, int64_t warp_stride,
+                                                 int4* stage_warp) {
+  const int lane = lane_id();
+  int4* my = stage_warp + lane * kStageInt4;
+  const int32_t* myw = reinterpret_cast<const int32_t*>(my);
+  for (int64_t base = warp_begin * 32; base < n_in; base += warp_stride * 32) {
+    const int64_t i = base + lane;
+    const bool active = i < n_in;
+    int32_t v = 0;
+    int64_t s = 0, e = 0;
+    int off = -1;
+    if (active) {
+      v = ld<false>(wl_in + i);
+      row_range(g, v, s, e);
+      off = stage_row(g, s, e, my);
+    }
+    cp_async_wait_all();
+    uint32_t m = kOut;
+    if (active) {
+      m = ld<NC>(T + v);
+      if (off >= 0) {
+        const int len = (int)(e - s);
+#pragma unroll
+        for (int k = 0; k < kLaneRowMax; k++)
+          if (k < len) m = min(m, ld<NC>(T + myw[off + k]));
+      } else {
+        visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) { m = min(m, ld<NC>(T + w)); });
+      }
+    }
+    bool keep = false;
+    if (active) {
+      if (m == kIn) m = kOut;
+      M[v] = m;
+      keep = m != kOut;
+    }
+    warp_append(keep, v, wl_out, cnt_out);
+    if (dsum != nullptr) warp_accumulate(e - s, dsum);
+  }
+}
+
+template <typename I, bool NC>
+__device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t* T, const uint32_t* M,
+                                                 const int32_t* wl_in, int n_in, int32_t* wl_out, int32_t* cnt_out,
+                                                 int64_t* dsum, const PrioCfg& p, uint32_t next_iter,
+                                                 int64_t warp_begin, int64_t warp_stride, int4* stage_warp) {
+  const int lane = lane_id();
+  int4* my = stage_warp + lane * kStageInt4;
+  const int32_t* myw = reinterpret_cast<const int32_t*>(my);
+  for (int64_t base = warp_begin * 32; base < n_in; base += warp_stride * 32) {
+    const int64_t i = base + lane;
+    const bool active = i < n_in;
+    int32_t v = 0;
+    int64_t s = 0, e = 0;
+    int off = -1;
+    if (active) {
+      v = ld<false>(wl_in + i);
+      row_range(g, v, s, e);
+      off = stage_row(g, s, e, my);
+    }
+    cp_async_wait_all();
+    bool keep = false;
+    if (active) {
+      const uint32_t t = ld<false>(T + v);
+      const uint32_t mv = ld<NC>(M + v);
+      bool any_out = mv == kOut, all_eq = mv == t;
+      if (off >= 0) {
+        const int len = (int)(e - s);
+#pragma unroll
+        for (int k = 0; k < kLaneRowMax; k++) {
+          if (k < len) {
+            const uint32_t mw = ld<NC>(M + myw[off + k]);
+            any_out |= mw == kOut;
+            all_eq &= (mw == t) | (mw == 0u);
+          }
+        }
+      } else {
+        visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) {
+          const uint32_t mw = ld<NC>(M + w);
+          any_out |= mw == kOut;
+          all_eq &= (mw == t) | (mw == 0u);
+        });
+      }
+      uint32_t nt;
+      if (any_out) {
+        nt = kOut;
+      } else if (all_eq) {
+        nt = kIn;
+      } else {
+        nt = make_tuple(p, next_iter, (uint32_t)v);
+        keep = true;
+      }
+      T[v] = nt;
+    }
+    warp_append(keep, v, wl_out, cnt_out);
+    if (dsum != nullptr) warp_accumulate(e - s, dsum);
+  }
+}
+
 template <int G, typename I, bool NC>
 __device__ __forceinline__ void column_group_rows(const GraphView<I>& g, const uint32_t* T, uint32_t* M,
                                                   const int32_t* wl_in, int n_in, int32_t* wl_out,

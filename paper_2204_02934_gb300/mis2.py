@@ -34,6 +34,10 @@ EXPORTS = [
     "mis2_config_default", "mis2_ctx_create", "mis2_ctx_destroy", "mis2_ctx_set_config", "mis2_get_stats",
     "mis2_run", "mis2_run_with_priorities", "mis2_aggregate", "mis2_coarsen", "mis2_coarsen_level",
     "mis2_coarsen_level_host", "mis2_status_string", "mis2_last_error", "mis2_version", "mis2_run_noalloc",
+    "mis2_batch_create", "mis2_batch_destroy", "mis2_batch_coarsen", "mis2_batch_level_sizes", "mis2_batch_labels",
+    "mis2_batch_coarse", "mis2_batch_stats",
+    "mis2_server_config_default", "mis2_server_create", "mis2_server_destroy", "mis2_server_submit",
+    "mis2_server_wait", "mis2_server_replay",
 ]
 MIS2_NOALLOC_MAX_N = 262144
 
@@ -59,7 +63,19 @@ class mis2_config(ctypes.Structure):
     _fields_ = [("hash_variant", ctypes.c_int32), ("agg_mode", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("warp_degree", ctypes.c_int32), ("block_degree", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("loop", ctypes.c_int32), ("debug_checks", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+                ("loop_blocks_per_sm", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
+
+
+class mis2_server_config(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
+                ("slot_max_n", ctypes.c_int64), ("slot_max_nnz", ctypes.c_int64), ("cfg", mis2_config)]
+
+
+class mis2_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("n_roots", ctypes.c_int64), ("n_aggs", ctypes.c_int64), ("c_nnz", ctypes.c_int64),
+                ("checksum", ctypes.c_uint64), ("t_arrive", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("status", ctypes.c_int32), ("slot", ctypes.c_int32)]
 
 
 class mis2_stats(ctypes.Structure):
@@ -107,6 +123,19 @@ def _lib(build_if_missing: bool = False):
         "mis2_coarsen_level": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
         "mis2_coarsen_level_host": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
         "mis2_run_noalloc": (i32, [CSR, u64, P, P, pi64, pi32, P]),
+        "mis2_batch_create": (i32, [ctypes.POINTER(P), i32, i64, i64, CFG]),
+        "mis2_batch_destroy": (i32, [P]),
+        "mis2_batch_coarsen": (i32, [P, i32, CSR, u64, i64, i32, pi32, P]),
+        "mis2_batch_level_sizes": (i32, [P, i32, P, P, P]),
+        "mis2_batch_labels": (i32, [P, i32, i32, P, P]),
+        "mis2_batch_coarse": (i32, [P, i32, i32, P, P, i64, P]),
+        "mis2_batch_stats": (i32, [P, ctypes.POINTER(mis2_stats)]),
+        "mis2_server_config_default": (None, [ctypes.POINTER(mis2_server_config)]),
+        "mis2_server_create": (i32, [ctypes.POINTER(P), ctypes.POINTER(mis2_server_config)]),
+        "mis2_server_destroy": (i32, [P]),
+        "mis2_server_submit": (i32, [P, CSR, u64, pi64]),
+        "mis2_server_wait": (i32, [P, i64, ctypes.POINTER(mis2_result)]),
+        "mis2_server_replay": (i32, [P, i32, CSR, i64, P, P, u64, ctypes.POINTER(mis2_result), pi64]),
         "mis2_status_string": (ctypes.c_char_p, [i32]),
         "mis2_last_error": (ctypes.c_char_p, []),
         "mis2_version": (ctypes.c_char_p, []),
@@ -350,3 +379,169 @@ class Context:
                                         stream)
         return dict(in_set=in_set[:dg.n], roots=roots[:nr], labels=labels[:dg.n], n_aggs=na,
                     c_rowptr=c_rowptr[:na + 1], c_colind=c_colind[:cn])
+
+
+# --------------------------------------------------------------- batches
+def mis2_batch_create(max_graphs: int, max_total_n: int, max_total_nnz: int, cfg: mis2_config | None = None):
+    h = ctypes.c_void_p()
+    _check(_lib().mis2_batch_create(ctypes.byref(h), max_graphs, max_total_n, max_total_nnz,
+                                    ctypes.byref(cfg) if cfg else None), "mis2_batch_create")
+    return h
+
+
+def mis2_batch_destroy(b) -> None:
+    _check(_lib().mis2_batch_destroy(b), "mis2_batch_destroy")
+
+
+def mis2_batch_coarsen(b, graphs, seed: int, min_n: int, max_levels: int, stream=None) -> int:
+    arr = (mis2_csr * len(graphs))(*graphs)
+    nl = ctypes.c_int32(0)
+    _check(_lib().mis2_batch_coarsen(b, len(graphs), arr, seed, min_n, max_levels, ctypes.byref(nl),
+                                     _stream(stream)), "mis2_batch_coarsen")
+    return nl.value
+
+
+def mis2_batch_level_sizes(b, level: int, n_graphs: int):
+    """Returns (n, n_aggs, c_nnz) per graph at `level`."""
+    n = np.zeros(n_graphs, np.int64)
+    na = np.zeros(n_graphs, np.int64)
+    cn = np.zeros(n_graphs, np.int64)
+    _check(_lib().mis2_batch_level_sizes(b, level, _ptr(n), _ptr(na), _ptr(cn)), "mis2_batch_level_sizes")
+    return n, na, cn
+
+
+def mis2_batch_labels(b, level: int, graph: int, labels, stream=None) -> None:
+    _check(_lib().mis2_batch_labels(b, level, graph, _ptr(labels), _stream(stream)), "mis2_batch_labels")
+
+
+def mis2_batch_coarse(b, level: int, graph: int, c_rowptr, c_colind, c_colind_cap: int, stream=None) -> None:
+    _check(_lib().mis2_batch_coarse(b, level, graph, _ptr(c_rowptr), _ptr(c_colind), c_colind_cap,
+                                    _stream(stream)), "mis2_batch_coarse")
+
+
+def mis2_batch_stats(b) -> mis2_stats:
+    st = mis2_stats()
+    _check(_lib().mis2_batch_stats(b, ctypes.byref(st)), "mis2_batch_stats")
+    return st
+
+
+class Batch:
+    """Owns a mis2_batch: coarsen many graphs' hierarchies together."""
+
+    def __init__(self, max_graphs: int, max_total_n: int, max_total_nnz: int, cfg: mis2_config | None = None,
+                 **overrides):
+        cfg = cfg or mis2_config_default()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.handle = mis2_batch_create(max_graphs, max_total_n, max_total_nnz, cfg)
+        self.n_graphs = 0
+        self.n_levels = 0
+
+    def close(self):
+        if self.handle:
+            mis2_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def coarsen(self, dgraphs, seed: int = 0, min_n: int = 1000, max_levels: int = 32, stream=None) -> int:
+        self._keep = dgraphs
+        self.n_graphs = len(dgraphs)
+        self.n_levels = mis2_batch_coarsen(self.handle, [d.csr for d in dgraphs], seed, min_n, max_levels, stream)
+        return self.n_levels
+
+    def level_sizes(self, level: int):
+        return mis2_batch_level_sizes(self.handle, level, self.n_graphs)
+
+    def labels(self, level: int, graph: int, device="cuda"):
+        import torch
+
+        n, _, _ = self.level_sizes(level)
+        out = torch.empty(max(int(n[graph]), 1), dtype=torch.int32, device=device)
+        mis2_batch_labels(self.handle, level, graph, out)
+        return out[:int(n[graph])]
+
+    def coarse(self, level: int, graph: int, device="cuda"):
+        import torch
+
+        n, na, cn = self.level_sizes(level)
+        c_rowptr = torch.empty(int(na[graph]) + 1, dtype=torch.int32, device=device)
+        cap = max(int(cn[graph]), 1)
+        c_colind = torch.empty(cap, dtype=torch.int32, device=device)
+        mis2_batch_coarse(self.handle, level, graph, c_rowptr, c_colind, cap)
+        return c_rowptr, c_colind[:int(cn[graph])]
+
+    def stats(self) -> mis2_stats:
+        return mis2_batch_stats(self.handle)
+
+
+# --------------------------------------------------------------- serving
+def mis2_server_config_default() -> mis2_server_config:
+    c = mis2_server_config()
+    _lib().mis2_server_config_default(ctypes.byref(c))
+    return c
+
+
+def mis2_server_create(cfg: mis2_server_config):
+    h = ctypes.c_void_p()
+    _check(_lib().mis2_server_create(ctypes.byref(h), ctypes.byref(cfg)), "mis2_server_create")
+    return h
+
+
+def mis2_server_destroy(s) -> None:
+    _check(_lib().mis2_server_destroy(s), "mis2_server_destroy")
+
+
+def mis2_server_submit(s, g_host: mis2_csr, seed: int = 0) -> int:
+    t = ctypes.c_int64(0)
+    _check(_lib().mis2_server_submit(s, ctypes.byref(g_host), seed, ctypes.byref(t)), "mis2_server_submit")
+    return t.value
+
+
+def mis2_server_wait(s, ticket: int) -> mis2_result:
+    r = mis2_result()
+    _check(_lib().mis2_server_wait(s, ticket, ctypes.byref(r)), "mis2_server_wait")
+    return r
+
+
+def mis2_server_replay(s, pool, arrival_s, pool_index, seed: int = 0):
+    """pool: list of host mis2_csr.  Returns (list of mis2_result, max in flight)."""
+    arr = (mis2_csr * len(pool))(*pool)
+    arrival = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    idx = np.ascontiguousarray(pool_index, dtype=np.int32)
+    res = (mis2_result * len(arrival))()
+    mif = ctypes.c_int64(0)
+    _check(_lib().mis2_server_replay(s, len(pool), arr, len(arrival), _ptr(arrival), _ptr(idx), seed, res,
+                                     ctypes.byref(mif)), "mis2_server_replay")
+    return list(res), mif.value
+
+
+class Server:
+    """Owns a mis2_server (continuous-batching request loop)."""
+
+    def __init__(self, slots=4, mem_budget=8 << 30, slot_max_n=1 << 22, slot_max_nnz=1 << 25, **cfg_overrides):
+        c = mis2_server_config_default()
+        c.slots, c.mem_budget, c.slot_max_n, c.slot_max_nnz = slots, mem_budget, slot_max_n, slot_max_nnz
+        for k, v in cfg_overrides.items():
+            setattr(c.cfg, k, v)
+        self.cfg = c
+        self.handle = mis2_server_create(c)
+
+    def close(self):
+        if self.handle:
+            mis2_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def replay(self, pool_host, arrival_s, pool_index, seed: int = 0):
+        return mis2_server_replay(self.handle, pool_host, arrival_s, pool_index, seed)

@@ -1,0 +1,101 @@
+"""Serving with continuous batching: every request's result is the same alone
+and in the mix (and equal to the oracle's), requests really overlap, and the
+memory budget gates admission."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2204_02934_gb300 import graphgen as gg
+from paper_2204_02934_gb300 import mis2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_02934_gb300 import _build
+
+    _build.build()
+
+
+def _fnv(h, arr):
+    for byte in np.ascontiguousarray(arr, dtype="<i4").tobytes():
+        h ^= byte
+        h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+def _oracle_checksum(g, seed):
+    lv = oracle.coarsen_level(g, seed=seed)
+    h = 1469598103934665603
+    for a in (lv.roots, lv.labels, lv.c_rowptr.astype(np.int32), lv.c_colind):
+        h = _fnv(h, a)
+    return h, lv
+
+
+def _pool():
+    graphs = [gg.grid3d_7pt(s, s, s) for s in (10, 14, 19, 25)]
+    graphs += [gg.rmat(sc, 8, seed=sc, rowptr_dtype=np.int32) for sc in (9, 10, 11, 12)]
+    graphs += [gg.grid2d_5pt(40, 37), gg.rgg2d(3000, 10.0, 3)]
+    keep = [(np.ascontiguousarray(g.rowptr), np.ascontiguousarray(g.colind)) for g in graphs]
+    host = [mis2.host_csr(rp, ci, g.n) for g, (rp, ci) in zip(graphs, keep)]
+    return graphs, keep, host
+
+
+def test_results_same_alone_and_in_the_mix():
+    graphs, keep, host = _pool()
+    n_req = 80
+    idx = (np.arange(n_req) * 7) % len(graphs)
+    arrivals = gg.poisson_arrivals(n_req, 2000.0, seed=4)
+    expect = [_oracle_checksum(g, 3)[0] for g in graphs]
+    results = {}
+    for slots in (1, 4):
+        srv = mis2.Server(slots=slots, slot_max_n=20000, slot_max_nnz=200000)
+        res, mif = srv.replay(host, arrivals, idx, seed=3)
+        srv.close()
+        assert all(r.status == 0 for r in res)
+        results[slots] = res
+        for r, gi in zip(res, idx):
+            assert r.checksum == expect[gi], "result differs from the oracle"
+        if slots == 1:
+            assert mif == 1
+    # same bits alone (1 slot) and in the mix (4 slots)
+    assert [r.checksum for r in results[1]] == [r.checksum for r in results[4]]
+
+
+def test_requests_overlap_when_they_arrive_together():
+    graphs, keep, host = _pool()
+    n_req = 32
+    idx = np.arange(n_req) % len(graphs)
+    srv = mis2.Server(slots=4, slot_max_n=20000, slot_max_nnz=200000)
+    res, mif = srv.replay(host, np.zeros(n_req), idx, seed=1)
+    srv.close()
+    assert mif >= 2
+    starts = sorted((r.t_start, r.t_done) for r in res)
+    overlapped = any(b[0] < a[1] for a, b in zip(starts, starts[1:]))
+    assert overlapped
+
+
+def test_memory_budget_limits_admission():
+    graphs, keep, host = _pool()
+    big = int(np.argmax([g.nnz for g in graphs]))
+    one = graphs[big]
+    need = (one.n + 1) * 4 + 4 * one.nnz + one.n * 9 + 4 * (one.n + 1) + 4 * one.nnz
+    srv = mis2.Server(slots=4, mem_budget=need + need // 2, slot_max_n=20000, slot_max_nnz=200000)
+    res, mif = srv.replay(host, np.zeros(8), np.full(8, big), seed=0)
+    srv.close()
+    assert mif == 1, "budget admits one copy of the largest request at a time"
+    assert len({r.checksum for r in res}) == 1
+
+
+def test_oversize_request_is_refused():
+    graphs, keep, host = _pool()
+    srv = mis2.Server(slots=1, slot_max_n=100, slot_max_nnz=1000)
+    with pytest.raises(mis2.Mis2Error) as e:
+        mis2.mis2_server_submit(srv.handle, host[3], 0)
+    assert e.value.status == -2
+    srv.close()
