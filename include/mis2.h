@@ -89,7 +89,7 @@ typedef struct {
   int32_t loop;           /* MIS2_LOOP_*; default DEVICE */
   int32_t debug_checks;   /* validate CSR and roots (extra passes); default 0 */
   int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
-  int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = as many as fit (max 4) */
+  int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = default (2) */
   int64_t spin_limit;     /* polls before a device barrier reports MIS2_ERR_TIMEOUT */
 } mis2_config;
 
@@ -98,6 +98,7 @@ typedef struct {
  * sizes and summed row lengths at the start of MIS-2 round r (phase-1 MIS-2
  * in trace, phase-2 MIS-2 in trace2), up to MIS2_TRACE_CAP rounds. */
 #define MIS2_TRACE_CAP 64
+#define MIS2_LOOP_TS_WORDS (4 + 4 * MIS2_TRACE_CAP)
 #define MIS2_NUM_KERNEL_CLASSES 8
 typedef struct {
   int32_t rounds;           /* rounds of the phase-1 MIS-2 (Algorithm 1 loop count) */
@@ -114,6 +115,11 @@ typedef struct {
   double kernel_ms[MIS2_NUM_KERNEL_CLASSES];
   int64_t kernel_launches[MIS2_NUM_KERNEL_CLASSES];
   int64_t launches;         /* CUDA kernels launched by the last call (always counted) */
+  /* device loop with timing: globaltimer ns of [0] the launch start, then per
+   * grid barrier b (b = 0 after set-up, 2r+1 after round r's column step,
+   * 2r+2 after its decide step) the last block's arrival [2+2b] and block 0's
+   * departure [3+2b]; one row per MIS-2 (phase-1, phase-2) */
+  int64_t loop_ns[2][MIS2_LOOP_TS_WORDS];
 } mis2_stats;
 
 typedef struct mis2_ctx mis2_ctx;

@@ -130,10 +130,9 @@ template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
                                                         const int32_t* left, const int32_t* left_cnt, int32_t* labels,
                                                         int32_t* err) {
-  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   const int lane = lane_id();
-  int4* my = stage[threadIdx.x >> 5] + lane * kStageInt4;
-  int32_t* myw = reinterpret_cast<int32_t*>(my);
+  int32_t* area = stage[threadIdx.x >> 5];
   const int64_t cnt = *left_cnt;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -142,27 +141,26 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
     const bool active = i < cnt;
     int32_t v = 0;
     int64_t s = 0, e = 0;
-    int off = -1;
     if (active) {
       v = left[i];
       row_range(g, v, s, e);
-      off = stage_row(g, s, e, my);
     }
-    cp_async_wait_all();
-    if (!active) continue;
-    const int len = (int)(e - s);
+    const int len = active ? (int)(e - s < kLaneRowMax ? e - s : kLaneRowMax) : -1;  // leftovers here have <= 32 entries
+    // this lane's row (staged), overwritten below with its labels
+    int32_t* myw = const_cast<int32_t*>(stage_rows_warp(g.colind, g.nnz, g.vec, s, len, area));
     int32_t lab[kLaneRowMax];
 #pragma unroll
     for (int j = 0; j < kLaneRowMax; j++) {
       int32_t t = -1;
       if (j < len) {
-        const int32_t w = off >= 0 ? myw[off + j] : g.colind[s + j];
+        const int32_t w = myw[j];
         t = w != v ? tent[w] : -1;
       }
       lab[j] = t;
     }
 #pragma unroll
-    for (int j = 0; j < kLaneRowMax; j++) myw[j] = lab[j];  // own slot only: no other lane reads it
+    for (int j = 0; j < kLaneRowMax; j++)
+      if (j < len) myw[j] = lab[j];  // own row only: rows of other lanes may follow it
     int32_t best = -1;
     int bc = 0, bs = 0;
     for (int j = 0; j < len; j++) {
@@ -183,8 +181,11 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
         bs = sz;
       }
     }
-    labels[v] = best;
-    if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
+    if (active) {
+      labels[v] = best;
+      if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
+    }
+    __syncwarp();
   }
 }
 

@@ -144,6 +144,7 @@ static int alloc_scratch(mis2_ctx* c) {
     }
   MIS2_TRY(dev_alloc(c, &s.ctr, kCtrWords));
   MIS2_TRY(dev_alloc(c, &s.dtrace, 2 * MIS2_TRACE_CAP * 4));
+  MIS2_TRY(dev_alloc(c, &s.loop_ts, 2 * kLoopTsWords));
   MIS2_TRY(dev_alloc(c, &s.tile, n / 2048 + 4));
   MIS2_TRY(dev_alloc(c, &s.roots2, n));
   MIS2_TRY(dev_alloc(c, &s.qlist, n));
@@ -165,6 +166,7 @@ static int alloc_scratch(mis2_ctx* c) {
   MIS2_TRY(dev_alloc(c, &s.tmp, nnz + 4));
   MIS2_TRY(dev_alloc(c, &s.labels_tmp, n));
   MIS2_TRY(dev_alloc(c, &s.bitmaps, (int64_t)coarse_bitmap_blocks(c) * ((n + 31) / 32)));
+  MIS2_TRY(dev_alloc(c, &s.chunk_off, n + 1));
   if (cudaMallocHost(&c->h_ctr, kCtrWords * sizeof(int32_t)) != cudaSuccess) return MIS2_ERR_OUT_OF_MEMORY;
   if (cudaMallocHost(&c->h_trace, 2 * MIS2_TRACE_CAP * 4 * sizeof(int64_t)) != cudaSuccess)
     return MIS2_ERR_OUT_OF_MEMORY;
@@ -174,6 +176,7 @@ static int alloc_scratch(mis2_ctx* c) {
 
 static void begin_call(mis2_ctx* c) {
   c->launches = 0;
+  memset(c->stats.loop_ns, 0, sizeof(c->stats.loop_ns));
   timer_reset(c);
   memset(c->stats.kernel_ms, 0, sizeof(c->stats.kernel_ms));
   memset(c->stats.kernel_launches, 0, sizeof(c->stats.kernel_launches));

@@ -4,17 +4,15 @@
 //
 // No global sort: vertices are bucketed by aggregate (counting sort), then
 // each aggregate's neighbour labels are de-duplicated on chip.
-//   - Aggregates whose members hold <= kWarpEntries entries: one warp.  A
-//     first walk finds the label range and count; a narrow range (<= 4096
-//     ids) goes through a shared-memory bitmap read out in order, few
-//     entries (<= 1024) through a shared-memory bitonic sort.
-//   - Everything else: one block with a global bitmap over all aggregate
-//     ids.  Each first-time bit flip appends the label to a discovery list;
-//     the list (the coarse row, unordered) is sorted in shared memory when it
-//     fits, otherwise the bitmap is read out in order.  Bits are cleared
-//     again, so the bitmap stays zero between aggregates.
-// Member rows of <= 32 entries are staged lane-per-row with asynchronous
-// copies; longer rows are walked by the whole warp.
+//   - Aggregates whose members hold <= kWarpEntries entries and have at
+//     most kDistinctCap coarse neighbours: one warp with a shared-memory hash
+//     set; the distinct labels are sorted on chip.
+//   - Everything else: a global bitmap over all aggregate ids per aggregate,
+//     filled by the whole grid 32 members at a time, then read out in order
+//     by one block (k_large_or / k_large_emit).
+// Member rows of <= 32 entries are staged in shared memory by the warp (one
+// coalesced copy per row) and read lane-per-row; longer rows are walked by
+// the whole warp.
 // Rows land in a scratch buffer at the aggregate's degree-sum offset, then
 // are packed behind the prefix sum of the row lengths.
 #include <algorithm>
@@ -26,11 +24,8 @@
 namespace mis2 {
 
 constexpr int kCoarseWarps = 4;        // warps per block of the warp-per-aggregate kernel
-constexpr int kBitmapWords = 128;      // 4096 ids per warp
 constexpr int kSortCap = 1024;         // entries per warp
 constexpr int kWarpEntries = 8192;     // larger aggregates go to the block kernel
-constexpr int kBlockSortCap = 8192;    // discovery lists sorted in shared memory up to this size
-static_assert(kBlockSortCap * 4 <= (kBlock / 32) * kStageWarpInt4 * 16, "sort buffer reuses the staging area");
 
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_hist(GraphView<I> g, const int32_t* labels, int32_t* agg_cnt,
@@ -41,11 +36,23 @@ __global__ void __launch_bounds__(kBlock) k_coarse_hist(GraphView<I> g, const in
     const int64_t v = base + lane;
     const int32_t a = v < g.n ? labels[v] : -1;
     const unsigned peers = __match_any_sync(kFull, a);
+    int deg = 0;
     if (a >= 0) {
-      if (lane == __ffs(peers) - 1) atomicAdd(agg_cnt + a, __popc(peers));
       int64_t s, e;
       row_range(g, v, s, e);
-      if (e > s) atomicAdd(ub + a, (int32_t)(e - s));
+      deg = (int)(e - s);
+    }
+    // sum of the degrees of the lanes holding the same label (one atomic per
+    // label per warp: an aggregate can hold millions of vertices)
+    int sum = 0;
+#pragma unroll
+    for (int src = 0; src < 32; src++) {
+      const int x = __shfl_sync(kFull, deg, src);
+      if ((peers >> src) & 1u) sum += x;
+    }
+    if (a >= 0 && lane == __ffs(peers) - 1) {
+      atomicAdd(agg_cnt + a, __popc(peers));
+      if (sum > 0) atomicAdd(ub + a, sum);
     }
   }
 }
@@ -66,236 +73,216 @@ __global__ void __launch_bounds__(kBlock) k_coarse_scatter(int64_t n, const int3
   }
 }
 
-// Walk every fine entry of aggregate a (members [mb, me)) with one warp and
-// call f(label) for each neighbour label != a.  Warp-uniform; f runs in the
-// lane that holds the entry.
-template <typename I, typename F>
+// Walk every fine entry of aggregate a (members [mb, me)) with one warp.
+// fb(lab) receives a register array of neighbour labels, -1 where the entry
+// is absent or belongs to a itself; every lane calls it with its own array
+// (32 entries for a staged member row, 4 per step of a long row), so a
+// callback can issue all its memory operations before waiting on any.
+template <typename I, typename FB>
 __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int32_t* labels, const int32_t* members,
-                                               int64_t mb, int64_t me, int32_t a, int4* stage_warp, F&& f) {
+                                               int64_t mb, int64_t me, int32_t a, int32_t* stage_warp, FB&& fb) {
   const int lane = lane_id();
-  int4* my = stage_warp + lane * kStageInt4;
-  const int32_t* myw = reinterpret_cast<const int32_t*>(my);
   for (int64_t kb = mb; kb < me; kb += 32) {
     const int64_t k = kb + lane;
     int64_t s = 0, e = 0;
-    int off = -1;
     const bool has = k < me;
-    if (has) {
-      row_range(g, members[k], s, e);
-      off = stage_row(g, s, e, my);
-    }
-    cp_async_wait_all();
-    if (off >= 0) {
-      const int len = (int)(e - s);
+    if (has) row_range(g, members[k], s, e);
+    const int len = has && e - s <= kLaneRowMax ? (int)(e - s) : -1;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
+    if (len > 0) {
       int32_t lab[kLaneRowMax];
 #pragma unroll
-      for (int j = 0; j < kLaneRowMax; j++) lab[j] = j < len ? labels[myw[off + j]] : a;
-#pragma unroll
-      for (int j = 0; j < kLaneRowMax; j++)
-        if (lab[j] != a) f(lab[j]);
+      for (int j = 0; j < kLaneRowMax; j++) {
+        const int32_t l = j < len ? labels[mine[j]] : a;
+        lab[j] = l != a ? l : -1;
+      }
+      fb(lab);
     }
-    unsigned longm = __ballot_sync(kFull, has && off < 0);
+    __syncwarp();
+    unsigned longm = __ballot_sync(kFull, has && len < 0);
     while (longm) {
       const int j = __ffs(longm) - 1;
       longm &= longm - 1;
       const int64_t sj = __shfl_sync(kFull, s, j), ej = __shfl_sync(kFull, e, j);
-      visit_row<32>(g.colind, g.nnz, sj, ej, lane, g.vec, [&](int32_t w) {
-        const int32_t l = labels[w];
-        if (l != a) f(l);
-      });
+      for (int64_t p = (sj & ~int64_t(3)) + 4 * lane; p < ej; p += 128) {
+        int32_t w4[4];
+        if (g.vec && p + 4 <= g.nnz) {
+          const int4 q = __ldg(reinterpret_cast<const int4*>(g.colind + p));
+          w4[0] = q.x, w4[1] = q.y, w4[2] = q.z, w4[3] = q.w;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 4; t++) w4[t] = (p + t >= sj && p + t < ej) ? g.colind[p + t] : 0;
+        }
+        int32_t lab[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+          const int32_t l = (p + t >= sj && p + t < ej) ? labels[w4[t]] : a;
+          lab[t] = l != a ? l : -1;
+        }
+        fb(lab);
+      }
     }
   }
 }
+
+// Warp per aggregate: insert every neighbour label into a shared-memory hash
+// set (256 slots, linear probing); first insertions form the distinct list,
+// which is then sorted (bitonic, a few dozen entries) and written out.  An
+// aggregate with more than kDistinctCap distinct labels goes to the large
+// path instead.
+constexpr int kHashSlots = 256;
+constexpr int kDistinctCap = 192;
+static_assert(kHashSlots + 256 <= kSortCap, "hash table and distinct list share the warp buffer");
+
+__device__ __forceinline__ uint32_t label_hash(int32_t l) { return ((uint32_t)l * 2654435761u) >> 24; }
 
 template <typename I>
 __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
     GraphView<I> g, const int32_t* labels, int64_t n_aggs, const int32_t* agg_ptr, const int32_t* members,
     const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt, int32_t* large, int32_t* large_cnt) {
   __shared__ int32_t sbuf[kCoarseWarps][kSortCap];
-  __shared__ int4 stage[kCoarseWarps][kStageWarpInt4];
+  __shared__ __align__(16) int32_t stage[kCoarseWarps][kStageWarpWords];
   __shared__ int32_t scnt[kCoarseWarps];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
-  int32_t* buf = sbuf[wib];
+  int32_t* tab = sbuf[wib];
+  int32_t* dl = sbuf[wib] + kHashSlots;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
     if (ub[a] > kWarpEntries) {
       if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
       continue;
     }
+    for (int j = lane; j < kHashSlots; j += 32) tab[j] = -1;
+    if (lane == 0) scnt[wib] = 0;
+    __syncwarp();
     const int64_t mb = agg_ptr[a], me = agg_ptr[a + 1];
-    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
-    int cnt = 0;
-    walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](int32_t l) {
-      lo = min(lo, (uint32_t)l);
-      hi = max(hi, (uint32_t)l);
-      cnt++;
-    });
-    lo = __reduce_min_sync(kFull, lo);
-    hi = __reduce_max_sync(kFull, hi);
-    cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
-    const int64_t out = ub_ptr[a];
-    if (cnt == 0) {
-      if (lane == 0) c_cnt[a] = 0;
-      continue;
-    }
-    if (hi - lo < 32u * kBitmapWords) {
-      uint32_t* bm = reinterpret_cast<uint32_t*>(buf);
-      for (int j = lane; j < kBitmapWords; j += 32) bm[j] = 0u;
-      __syncwarp();
-      walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](int32_t l) {
-        const uint32_t d = (uint32_t)l - lo;
-        atomicOr(bm + (d >> 5), 1u << (d & 31));
-      });
-      __syncwarp();
-      constexpr int WPL = kBitmapWords / 32;  // words per lane
-      uint32_t wv[WPL];
-      int pc = 0;
+    walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](auto& lab) {
+      int32_t prev = -1;
 #pragma unroll
-      for (int q = 0; q < WPL; q++) {
-        wv[q] = bm[lane * WPL + q];
-        pc += __popc(wv[q]);
-      }
-      int incl = pc;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-      }
-      int pos = incl - pc;
-#pragma unroll
-      for (int q = 0; q < WPL; q++) {
-        uint32_t w = wv[q];
-        while (w) {
-          const int bit = __ffs(w) - 1;
-          w &= w - 1;
-          tmp[out + pos++] = (int32_t)(lo + (uint32_t)((lane * WPL + q) * 32 + bit));
+      for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++) {
+        const int32_t l = lab[j];
+        if (l < 0 || l == prev) continue;
+        prev = l;
+        uint32_t h = label_hash(l);
+        for (int probe = 0; probe < kHashSlots; probe++) {
+          const int32_t old = atomicCAS(tab + h, -1, l);
+          if (old == -1) {
+            const int p = atomicAdd(scnt + wib, 1);
+            if (p < kDistinctCap) dl[p] = l;
+            break;
+          }
+          if (old == l) break;
+          h = (h + 1) & (kHashSlots - 1);
         }
       }
-      const int total = __shfl_sync(kFull, incl, 31);
-      if (lane == 0) c_cnt[a] = total;
+    });
+    __syncwarp();
+    const int D = scnt[wib];
+    if (D > kDistinctCap) {
+      if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
       __syncwarp();
       continue;
     }
-    if (cnt <= kSortCap) {
-      if (lane == 0) scnt[wib] = 0;
-      __syncwarp();
-      walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib],
-                        [&](int32_t l) { buf[atomicAdd(scnt + wib, 1)] = l; });
-      __syncwarp();
-      int P = 32;
-      while (P < cnt) P <<= 1;
-      for (int i = cnt + lane; i < P; i += 32) buf[i] = 0x7FFFFFFF;
-      __syncwarp();
-      for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = lane; i < P; i += 32) {
-            const int ixj = i ^ j;
-            if (ixj > i) {
-              const int32_t x = buf[i], y = buf[ixj];
-              const bool up = (i & k) == 0;
-              if ((x > y) == up) {
-                buf[i] = y;
-                buf[ixj] = x;
-              }
+    int P = 32;
+    while (P < D) P <<= 1;
+    for (int i = D + lane; i < P; i += 32) dl[i] = 0x7FFFFFFF;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < P; i += 32) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const int32_t x = dl[i], y = dl[ixj];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              dl[i] = y;
+              dl[ixj] = x;
             }
           }
-          __syncwarp();
         }
+        __syncwarp();
       }
-      int total = 0;
-      for (int base = 0; base < cnt; base += 32) {
-        const int i = base + lane;
-        const bool keep = i < cnt && (i == 0 || buf[i - 1] != buf[i]);
-        const unsigned b = __ballot_sync(kFull, keep);
-        if (keep) tmp[out + total + __popc(b & ((1u << lane) - 1u))] = buf[i];
-        total += __popc(b);
-      }
-      if (lane == 0) c_cnt[a] = total;
-      __syncwarp();
-      continue;
     }
-    if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
+    const int64_t out = ub_ptr[a];
+    for (int i = lane; i < D; i += 32) tmp[out + i] = dl[i];
+    if (lane == 0) c_cnt[a] = D;
+    __syncwarp();
   }
 }
 
-// Block per large aggregate; `bitmaps` holds one zeroed bitmap of `words`
-// words per block.
+// Large aggregates go through global bitmaps in batches of up to `slots`
+// aggregates: every warp of the grid ORs the labels of 32 members at a time
+// into its aggregate's bitmap (fire-and-forget atomics, so an aggregate of a
+// million members is spread over the whole GPU), then one block per
+// aggregate reads its bitmap out in order and clears it.
+
+// chunk_off[i] = number of 32-member chunks of the batch's aggregates < i.
+__global__ void k_large_chunks(const int32_t* large, int32_t k0, int32_t kb, const int32_t* agg_ptr,
+                               int64_t* chunk_off) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int64_t acc = 0;
+  for (int i = 0; i < kb; i++) {
+    chunk_off[i] = acc;
+    const int32_t a = large[k0 + i];
+    acc += (agg_ptr[a + 1] - agg_ptr[a] + 31) / 32;
+  }
+  chunk_off[kb] = acc;
+}
+
 template <typename I>
-__global__ void __launch_bounds__(kBlock) k_coarse_large(GraphView<I> g, const int32_t* labels,
-                                                         const int32_t* agg_ptr, const int32_t* members,
-                                                         const int32_t* ub_ptr, const int32_t* large,
-                                                         const int32_t* large_cnt, uint32_t* bitmaps, int64_t words,
-                                                         int32_t* tmp, int32_t* c_cnt) {
-  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
-  int32_t* sorted = reinterpret_cast<int32_t*>(&stage[0][0]);  // reused once the walk is done
-  __shared__ int disc;
-  __shared__ int sh[40];
-  uint32_t* bm = bitmaps + (int64_t)blockIdx.x * words;
-  const int64_t nl = *large_cnt;
-  const int lane = lane_id(), wib = threadIdx.x >> 5;
-  for (int64_t li = blockIdx.x; li < nl; li += gridDim.x) {
-    const int32_t a = large[li];
-    const int64_t mb = agg_ptr[a], me = agg_ptr[a + 1];
-    const int64_t out = ub_ptr[a];
-    if (threadIdx.x == 0) disc = 0;
-    __syncthreads();
-    // each warp walks a contiguous share of the members
-    const int64_t per = (me - mb + (kBlock / 32) - 1) / (kBlock / 32);
-    const int64_t w0 = mb + wib * per, w1 = min(me, w0 + per);
-    walk_aggregate<I>(g, labels, members, w0, max(w0, w1), a, stage[wib], [&](int32_t l) {
-      const uint32_t bit = 1u << (l & 31);
-      const uint32_t old = atomicOr(bm + (l >> 5), bit);
-      if ((old & bit) == 0u) tmp[out + atomicAdd(&disc, 1)] = l;
-    });
-    __syncthreads();
-    const int D = disc;
-    if (D <= kBlockSortCap) {
-      int P = 1;
-      while (P < D) P <<= 1;
-      for (int i = threadIdx.x; i < P; i += blockDim.x) sorted[i] = i < D ? tmp[out + i] : 0x7FFFFFFF;
-      __syncthreads();
-      for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            const int ixj = i ^ j;
-            if (ixj > i) {
-              const int32_t x = sorted[i], y = sorted[ixj];
-              const bool up = (i & k) == 0;
-              if ((x > y) == up) {
-                sorted[i] = y;
-                sorted[ixj] = x;
-              }
-            }
-          }
-          __syncthreads();
-        }
-      }
-      for (int i = threadIdx.x; i < D; i += blockDim.x) {
-        const int32_t l = sorted[i];
-        tmp[out + i] = l;
-        bm[l >> 5] = 0u;  // clear for the next aggregate (idempotent per word)
-      }
-    } else {
-      // read the whole bitmap out in order, clearing it
-      int64_t run = 0;
-      for (int64_t wb = 0; wb < words; wb += blockDim.x) {
-        const int64_t wi = wb + threadIdx.x;
-        uint32_t w = wi < words ? bm[wi] : 0u;
-        int total;
-        int pos = block_exclusive_scan(__popc(w), sh, &total);
-        if (w != 0u) bm[wi] = 0u;
-        while (w) {
-          const int bit = __ffs(w) - 1;
-          w &= w - 1;
-          tmp[out + run + pos++] = (int32_t)(wi * 32 + bit);
-        }
-        run += total;
-      }
+__global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32_t* labels, const int32_t* agg_ptr,
+                                                     const int32_t* members, const int32_t* large, int32_t k0,
+                                                     int32_t kb, const int64_t* chunk_off, uint32_t* bitmaps,
+                                                     int64_t words) {
+  __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
+  const int64_t total = chunk_off[kb];
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < total; ch += nw) {
+    int lo = 0, hi = kb;  // last i with chunk_off[i] <= ch
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (chunk_off[mid] <= ch) lo = mid;
+      else hi = mid;
     }
-    if (threadIdx.x == 0) c_cnt[a] = D;
-    __syncthreads();
+    const int32_t a = large[k0 + lo];
+    const int64_t mb = agg_ptr[a] + (ch - chunk_off[lo]) * 32;
+    const int64_t me = min((int64_t)agg_ptr[a + 1], mb + 32);
+    uint32_t* bm = bitmaps + (int64_t)lo * words;
+    walk_aggregate<I>(g, labels, members, mb, me, a, stage[threadIdx.x >> 5], [&](auto& lab) {
+#pragma unroll
+      for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++)
+        if (lab[j] >= 0) atomicOr(bm + (lab[j] >> 5), 1u << (lab[j] & 31));
+    });
   }
 }
+
+__global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int32_t k0, int32_t kb,
+                                                       const int32_t* ub_ptr, uint32_t* bitmaps, int64_t words,
+                                                       int32_t* tmp, int32_t* c_cnt) {
+  __shared__ int sh[40];
+  for (int i = blockIdx.x; i < kb; i += gridDim.x) {
+    const int32_t a = large[k0 + i];
+    uint32_t* bm = bitmaps + (int64_t)i * words;
+    const int64_t out = ub_ptr[a];
+    int64_t run = 0;
+    for (int64_t wb = 0; wb < words; wb += blockDim.x) {
+      const int64_t wi = wb + threadIdx.x;
+      uint32_t w = wi < words ? bm[wi] : 0u;
+      int total;
+      int pos = block_exclusive_scan(__popc(w), sh, &total);
+      if (w != 0u) bm[wi] = 0u;
+      while (w) {
+        const int bit = __ffs(w) - 1;
+        w &= w - 1;
+        tmp[out + run + pos++] = (int32_t)(wi * 32 + bit);
+      }
+      run += total;
+    }
+    if (threadIdx.x == 0) c_cnt[a] = (int32_t)run;
+  }
+}
+
+constexpr int kPackWarpMax = 4096;  // longer coarse rows are copied by the whole grid
 
 __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const int32_t* ub_ptr, const int32_t* c_cnt,
                                                         const int32_t* c_rowptr, const int32_t* tmp,
@@ -303,9 +290,28 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const in
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
-    const int64_t src = ub_ptr[a], dst = c_rowptr[a];
     const int len = c_cnt[a];
+    if (len > kPackWarpMax) continue;
+    const int64_t src = ub_ptr[a], dst = c_rowptr[a];
     for (int i = lane; i < len; i += 32) c_colind[dst + i] = tmp[src + i];
+  }
+}
+
+// Rows longer than kPackWarpMax (only large aggregates have them): every
+// block copies a slice of each.
+__global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* large, const int32_t* n_large,
+                                                             const int32_t* ub_ptr, const int32_t* c_cnt,
+                                                             const int32_t* c_rowptr, const int32_t* tmp,
+                                                             int32_t* c_colind) {
+  const int64_t nl = *n_large;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = 0; i < nl; i++) {
+    const int32_t a = large[i];
+    const int64_t len = c_cnt[a];
+    if (len <= kPackWarpMax) continue;
+    const int64_t src = ub_ptr[a], dst = c_rowptr[a];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += stride)
+      c_colind[dst + k] = tmp[src + k];
   }
 }
 
@@ -348,14 +354,31 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
   k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
                                                          s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge);
-  const int64_t words = (n_aggs + 31) / 32;
-  const int nb = coarse_bitmap_blocks(c);
-  MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)nb * words * sizeof(uint32_t), st));
-  k_coarse_large<I><<<nb, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.ub_ptr, s.large, s.ctr + kCtrLarge,
-                                           s.bitmaps, words, s.tmp, s.c_cnt);
-  c->launches += 3;
+  c->launches += 2;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
+  // large aggregates, in batches of `slots` bitmaps
+  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MIS2_CUDA(cudaStreamSynchronize(st));
+  const int32_t n_large = c->h_ctr[kCtrLarge];
+  if (n_large > 0) {
+    const int64_t words = (n_aggs + 31) / 32;
+    const int64_t words_cap = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
+    const int32_t slots = (int32_t)std::max<int64_t>(1, (int64_t)coarse_bitmap_blocks(c) * words_cap / words);
+    timer_begin(c, kKcCoarse, st);
+    for (int32_t k0 = 0; k0 < n_large; k0 += slots) {
+      const int32_t kb = std::min(slots, n_large - k0);
+      MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)kb * words * sizeof(uint32_t), st));
+      k_large_chunks<<<1, 32, 0, st>>>(s.large, k0, kb, s.agg_ptr, s.chunk_off);
+      k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, k0, kb,
+                                                        s.chunk_off, s.bitmaps, words);
+      k_large_emit<<<std::min<int32_t>(kb, c->sm_count * 2), kBlock, 0, st>>>(s.large, k0, kb, s.ub_ptr, s.bitmaps,
+                                                                             words, s.tmp, s.c_cnt);
+      c->launches += 3;
+    }
+    timer_end(c, st);
+    MIS2_CUDA(cudaGetLastError());
+  }
   MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MIS2_CUDA(cudaStreamSynchronize(st));
@@ -365,6 +388,11 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
                                                                         c_colind);
   c->launches++;
+  if (n_large > 0) {
+    k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
+                                                           s.tmp, c_colind);
+    c->launches++;
+  }
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   *c_nnz = total;

@@ -24,11 +24,19 @@ __device__ __forceinline__ void st_release_i32(int32_t* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *reinterpret_cast<const volatile int32_t*>(p); }
+__device__ __forceinline__ int64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return (int64_t)t;
+}
 
 // Sense-free generation barrier over all blocks of the grid.  Returns false
 // (in every thread of the block) when this block gave up waiting or another
 // block already reported a timeout.
-__device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t* gen, int32_t* err, int64_t spin_limit) {
+// ts (optional): the last block to arrive stores its arrival time in ts[0],
+// block 0 its departure time in ts[1] (globaltimer, ns).
+__device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t* gen, int32_t* err, int64_t spin_limit,
+                                             int64_t* ts = nullptr) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -37,6 +45,7 @@ __device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t* gen, int32
     const int arrived = atomicAdd(count, 1);
     ok = 1;
     if (arrived == (int)gridDim.x - 1) {
+      if (ts != nullptr) ts[0] = global_ns();
       atomicExch(count, 0);
       __threadfence();
       st_release_i32(gen, my_gen + 1);
@@ -52,6 +61,7 @@ __device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t* gen, int32
       }
     }
     __threadfence();
+    if (ts != nullptr && blockIdx.x == 0) ts[1] = global_ns();
   }
   __syncthreads();
   return ok != 0;
@@ -64,6 +74,7 @@ struct LoopArgs {
   uint32_t* M;
   int32_t* ctr;
   int64_t* dtr;  // trace of this MIS-2 (MIS2_TRACE_CAP x 4)
+  int64_t* ts;   // barrier timestamps (2 per barrier) or null
   const int32_t* labels;
   int64_t spin_limit;
   int32_t warp_degree;
@@ -75,8 +86,8 @@ struct LoopArgs {
 template <int G, typename I>
 __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
   __shared__ uint32_t sh[40];
-  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
-  int4* my_stage = stage[threadIdx.x >> 5];
+  __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
+  int32_t* my_stage = stage[threadIdx.x >> 5];
   int32_t* ctr = a.ctr;
   int32_t* bar_count = ctr + kCtrBarrier;
   int32_t* bar_gen = ctr + kCtrBarrier + 1;
@@ -87,7 +98,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg 
 
   mis_init_rows<I>(g, a.labels, p, a.T, a.M, a.wl1[0], a.wl2[0], ctr + ctr_c1(0, 0), ctr + ctr_c2(0, 0),
                    a.warp_degree, a.block_degree, tid, nthreads);
-  if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit)) return;
+  int64_t* ts = a.ts;
+  if (ts != nullptr && tid == 0) ts[0] = global_ns();  // start of the launch
+  if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts ? ts + 2 : nullptr)) return;
 
   int r = 0;
   for (;; r++) {
@@ -126,7 +139,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg 
     if (n2[2] > 0)
       column_block_rows<I, false>(g, a.T, a.M, in2.l[2], n2[2], out2.l[2], ctr + ctr_c2(nslot, 2), d2, blockIdx.x,
                                   gridDim.x, sh);
-    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit)) return;
+    const bool ts_on = ts != nullptr && r < MIS2_TRACE_CAP;
+    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr)) return;
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = w1;
@@ -142,7 +156,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg 
     if (n1[2] > 0)
       decide_block_rows<I, false>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
                                   (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
-    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit)) return;
+    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr)) return;
   }
   if (tid == 0) ctr[kCtrRounds] = r;
 }
@@ -153,7 +167,7 @@ static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cud
   int per_sm = 0;
   MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MIS2_ERR_CUDA;
-  const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 4;
+  const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 2;
   const int blocks = c->sm_count * std::min(per_sm, want);
   c->device_loop_blocks = blocks;
   void* args[] = {&gv, &p, &la};
@@ -183,6 +197,7 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.M = s.M;
   la.ctr = s.ctr;
   la.dtr = s.dtrace + (int64_t)trace_phase * MIS2_TRACE_CAP * 4;
+  la.ts = c->cfg.timing ? s.loop_ts + (int64_t)trace_phase * kLoopTsWords : nullptr;
   la.labels = labels;
   la.spin_limit = c->cfg.spin_limit;
   la.warp_degree = c->cfg.warp_degree;
@@ -208,6 +223,11 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   if (c->h_ctr[kCtrErr] & kErrTimeout) return MIS2_ERR_TIMEOUT;
   if (c->h_ctr[kCtrErr] & kErrNoProgress) return MIS2_ERR_NO_PROGRESS;
   *rounds = c->h_ctr[kCtrRounds];
+  if (la.ts != nullptr) {
+    MIS2_CUDA(cudaMemcpyAsync(c->stats.loop_ns[trace_phase], la.ts, kLoopTsWords * sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, st));
+    MIS2_CUDA(cudaStreamSynchronize(st));
+  }
   return MIS2_OK;
 }
 

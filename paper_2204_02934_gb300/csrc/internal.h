@@ -33,6 +33,7 @@ enum : int {
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 32;
+constexpr int kLoopTsWords = MIS2_LOOP_TS_WORDS;
 
 enum KernelClass : int {
   kKcInit = 0,
@@ -52,6 +53,7 @@ struct Scratch {
   int32_t* wl2[2][kClasses] = {};
   int32_t* ctr = nullptr;
   int64_t* dtrace = nullptr;  // [2][MIS2_TRACE_CAP][4]
+  int64_t* loop_ts = nullptr;  // [2][kLoopTsWords] device-loop barrier timestamps
   int32_t* tile = nullptr;
   int32_t* roots2 = nullptr;
   int32_t* qlist = nullptr;
@@ -71,7 +73,8 @@ struct Scratch {
   int32_t* c_cnt = nullptr;
   int32_t* large = nullptr;
   int32_t* tmp = nullptr;        // coarse rows before packing (max_nnz)
-  uint32_t* bitmaps = nullptr;   // coarse graph: one bitmap over aggregate ids per large-row block
+  uint32_t* bitmaps = nullptr;   // coarse graph: bitmaps over aggregate ids for large aggregates
+  int64_t* chunk_off = nullptr;  // coarse graph: member-chunk offsets of a batch of large aggregates
   int32_t* labels_tmp = nullptr; // labels when the caller passes none
 };
 

@@ -58,7 +58,7 @@ template <typename I>
 __global__ void __launch_bounds__(kBlock) k_column_lane(GraphView<I> g, const uint32_t* T, uint32_t* M,
                                                         const int32_t* wl_in, const int32_t* cnt_in, int32_t* wl_out,
                                                         int32_t* cnt_out, int32_t* zero, PhaseTrace tr) {
-  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kBlock) k_decide_lane(GraphView<I> g, uint32_t
                                                         const int32_t* wl_in, const int32_t* cnt_in, int32_t* wl_out,
                                                         int32_t* cnt_out, int32_t* zero, PhaseTrace tr, PrioCfg p,
                                                         uint32_t next_iter) {
-  __shared__ int4 stage[kBlock / 32][kStageWarpInt4];
+  __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;

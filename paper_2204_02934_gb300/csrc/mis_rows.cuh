@@ -26,57 +26,108 @@ struct RowLists {
   int32_t* l[kClasses];
 };
 
-// Lane-per-row rows (G = 1) stage their column indices in shared memory with
-// asynchronous 16-byte copies issued all at once, then issue every neighbour
-// gather back to back: a row costs about two memory latencies instead of one
-// per 16-byte chunk.
-constexpr int kLaneRowMax = 32;                          // entries staged per lane
-constexpr int kStageInt4 = (kLaneRowMax + 3) / 4 + 1;   // 9 int4 cover 32 entries at any alignment
-constexpr int kStageWarpInt4 = 32 * kStageInt4;
+// Lane-per-row rows (G = 1): the warp first copies the column indices of
+// its 32 rows into shared memory, one row at a time with 4-byte asynchronous
+// copies, so every copy instruction touches one or two cache lines (per-lane
+// loads of 32 different rows touch 32); then each lane issues its row's
+// neighbour gathers back to back from its own slot.
+constexpr int kLaneRowMax = 32;          // entries staged per row
+constexpr int kRowSlot = kLaneRowMax + 1;  // padded slot: lane i reads bank (i + k) % 32
+constexpr int kStageWarpWords = 32 * kRowSlot;
 
-// Stage colind[s, e) into `my`; returns the word offset of colind[s] inside
-// the staged words, or -1 when the row does not fit (too long, buffer not
-// 16-byte aligned, or the last 16-byte chunk would pass nnz).
-template <typename I>
-__device__ __forceinline__ int stage_row(const GraphView<I>& g, int64_t s, int64_t e, int4* my) {
-  if (!g.vec || e - s > kLaneRowMax) return -1;
-  const int64_t a = s & ~int64_t(3);
-  const int nq = (int)((e - a + 3) >> 2);
-  if (a + 4 * (int64_t)nq > g.nnz) return -1;
-#pragma unroll
-  for (int k = 0; k < kStageInt4; k++)
-    if (k < nq) cp_async16(my + k, g.colind + a + 4 * k);
-  return (int)(s - a);
+// Worklist appends of the lane-per-row passes collect in a per-warp
+// shared-memory buffer and reach the global list in batches: one atomic per
+// ~kAppendBuf entries instead of one per 32 rows.  (Every warp of the grid
+// appends to the same counter, and same-address atomics serialise.)
+constexpr int kAppendBuf = 256;
+constexpr int kWarpSmemWords = kStageWarpWords + kAppendBuf;
+
+struct WarpAppender {
+  int32_t* buf;
+  int32_t* list;
+  int32_t* cnt;
+  int n;
+  __device__ __forceinline__ void flush() {
+    __syncwarp();
+    if (n == 0) return;
+    const int lane = lane_id();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(cnt, n);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < n; i += 32) list[base + i] = buf[i];
+    __syncwarp();
+    n = 0;
+  }
+  // every lane of the warp calls this
+  __device__ __forceinline__ void push(bool want, int32_t v) {
+    const unsigned b = __ballot_sync(kFull, want);
+    if (want) buf[n + __popc(b & ((1u << lane_id()) - 1u))] = v;
+    n += __popc(b);
+    if (n > kAppendBuf - 32) flush();
+  }
+};
+
+// Stage each lane's row colind[s, s + len) (len <= kLaneRowMax, or len < 0:
+// not staged) in the warp's shared area and return where this lane's row
+// starts there.  When the 32 rows are back to back in colind (worklists that
+// still hold runs of consecutive vertices), the whole span moves with 16-byte
+// copies, 512 contiguous bytes per instruction; otherwise each row moves with
+// one coalesced 4-byte copy per entry, into padded per-lane slots.  Every
+// lane of the warp must call this; on return every staged row is visible to
+// its lane.  `nnz` bounds the 16-byte copies to the colind allocation.
+__device__ __forceinline__ const int32_t* stage_rows_warp(const int32_t* __restrict__ colind, int64_t nnz, bool vec,
+                                                          int64_t s, int len, int32_t* area) {
+  const int lane = lane_id();
+  const int64_t s_next = __shfl_down_sync(kFull, s, 1);
+  const int64_t e = s + (len > 0 ? len : 0);
+  const bool joined = lane == 31 || e == s_next;
+  const int64_t s0 = __shfl_sync(kFull, s, 0);
+  const int64_t e31 = __shfl_sync(kFull, e, 31);
+  const int64_t a = s0 & ~int64_t(3);
+  const int64_t nq = (e31 - a + 3) >> 2;
+  if (vec && __all_sync(kFull, len >= 0 && joined) && nq * 4 <= kStageWarpWords && a + nq * 4 <= nnz) {
+    for (int64_t q = lane; q < nq; q += 32) cp_async16(area + 4 * q, colind + a + 4 * q);
+    cp_async_wait_all();
+    __syncwarp();
+    return area + (s - a);
+  }
+#pragma unroll 4
+  for (int j = 0; j < 32; j++) {
+    const int64_t sj = __shfl_sync(kFull, s, j);
+    const int lj = __shfl_sync(kFull, len, j);
+    if (lane < lj) cp_async4(area + j * kRowSlot + lane, colind + sj + lane);
+  }
+  cp_async_wait_all();
+  __syncwarp();
+  return area + lane * kRowSlot;
 }
 
 template <typename I, bool NC>
 __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const uint32_t* T, uint32_t* M,
                                                  const int32_t* wl_in, int n_in, int32_t* wl_out, int32_t* cnt_out,
                                                  int64_t* dsum, int64_t warp_begin, int64_t warp_stride,
-                                                 int4* stage_warp) {
+                                                 int32_t* stage_warp) {
   const int lane = lane_id();
-  int4* my = stage_warp + lane * kStageInt4;
-  const int32_t* myw = reinterpret_cast<const int32_t*>(my);
+  WarpAppender app{stage_warp + kStageWarpWords, wl_out, cnt_out, 0};
+  int64_t dacc = 0;
   for (int64_t base = warp_begin * 32; base < n_in; base += warp_stride * 32) {
     const int64_t i = base + lane;
     const bool active = i < n_in;
     int32_t v = 0;
     int64_t s = 0, e = 0;
-    int off = -1;
     if (active) {
       v = ld<false>(wl_in + i);
       row_range(g, v, s, e);
-      off = stage_row(g, s, e, my);
     }
-    cp_async_wait_all();
+    const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
     uint32_t m = kOut;
     if (active) {
       m = ld<NC>(T + v);
-      if (off >= 0) {
-        const int len = (int)(e - s);
+      if (len >= 0) {
 #pragma unroll
         for (int k = 0; k < kLaneRowMax; k++)
-          if (k < len) m = min(m, ld<NC>(T + myw[off + k]));
+          if (k < len) m = min(m, ld<NC>(T + mine[k]));
       } else {
         visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) { m = min(m, ld<NC>(T + w)); });
       }
@@ -87,42 +138,43 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
       M[v] = m;
       keep = m != kOut;
     }
-    warp_append(keep, v, wl_out, cnt_out);
-    if (dsum != nullptr) warp_accumulate(e - s, dsum);
+    __syncwarp();  // slots are rewritten by the next iteration's copies
+    app.push(keep, v);
+    dacc += e - s;
   }
+  app.flush();
+  if (dsum != nullptr) warp_accumulate(dacc, dsum);
 }
 
 template <typename I, bool NC>
 __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t* T, const uint32_t* M,
                                                  const int32_t* wl_in, int n_in, int32_t* wl_out, int32_t* cnt_out,
                                                  int64_t* dsum, const PrioCfg& p, uint32_t next_iter,
-                                                 int64_t warp_begin, int64_t warp_stride, int4* stage_warp) {
+                                                 int64_t warp_begin, int64_t warp_stride, int32_t* stage_warp) {
   const int lane = lane_id();
-  int4* my = stage_warp + lane * kStageInt4;
-  const int32_t* myw = reinterpret_cast<const int32_t*>(my);
+  WarpAppender app{stage_warp + kStageWarpWords, wl_out, cnt_out, 0};
+  int64_t dacc = 0;
   for (int64_t base = warp_begin * 32; base < n_in; base += warp_stride * 32) {
     const int64_t i = base + lane;
     const bool active = i < n_in;
     int32_t v = 0;
     int64_t s = 0, e = 0;
-    int off = -1;
     if (active) {
       v = ld<false>(wl_in + i);
       row_range(g, v, s, e);
-      off = stage_row(g, s, e, my);
     }
-    cp_async_wait_all();
+    const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
     bool keep = false;
     if (active) {
       const uint32_t t = ld<false>(T + v);
       const uint32_t mv = ld<NC>(M + v);
       bool any_out = mv == kOut, all_eq = mv == t;
-      if (off >= 0) {
-        const int len = (int)(e - s);
+      if (len >= 0) {
 #pragma unroll
         for (int k = 0; k < kLaneRowMax; k++) {
           if (k < len) {
-            const uint32_t mw = ld<NC>(M + myw[off + k]);
+            const uint32_t mw = ld<NC>(M + mine[k]);
             any_out |= mw == kOut;
             all_eq &= (mw == t) | (mw == 0u);
           }
@@ -145,9 +197,12 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
       }
       T[v] = nt;
     }
-    warp_append(keep, v, wl_out, cnt_out);
-    if (dsum != nullptr) warp_accumulate(e - s, dsum);
+    __syncwarp();
+    app.push(keep, v);
+    dacc += e - s;
   }
+  app.flush();
+  if (dsum != nullptr) warp_accumulate(dacc, dsum);
 }
 
 template <int G, typename I, bool NC>
@@ -157,6 +212,7 @@ __device__ __forceinline__ void column_group_rows(const GraphView<I>& g, const u
                                                   int64_t warp_stride) {
   constexpr int RPW = 32 / G;
   const int lane = lane_id(), lg = lane & (G - 1), sub = lane / G;
+  int64_t dacc = 0;
   for (int64_t base = warp_begin * RPW; base < n_in; base += warp_stride * RPW) {
     const int64_t i = base + sub;
     const bool active = i < n_in;
@@ -179,8 +235,9 @@ __device__ __forceinline__ void column_group_rows(const GraphView<I>& g, const u
       keep = m != kOut;
     }
     warp_append(keep, v, wl_out, cnt_out);
-    if (dsum != nullptr) warp_accumulate(lg == 0 ? len : 0, dsum);
+    dacc += lg == 0 ? len : 0;
   }
+  if (dsum != nullptr) warp_accumulate(dacc, dsum);
 }
 
 template <int G, typename I, bool NC>
@@ -191,6 +248,7 @@ __device__ __forceinline__ void decide_group_rows(const GraphView<I>& g, uint32_
                                                   int64_t warp_stride) {
   constexpr int RPW = 32 / G;
   const int lane = lane_id(), lg = lane & (G - 1), sub = lane / G;
+  int64_t dacc = 0;
   for (int64_t base = warp_begin * RPW; base < n_in; base += warp_stride * RPW) {
     const int64_t i = base + sub;
     const bool active = i < n_in;
@@ -229,8 +287,9 @@ __device__ __forceinline__ void decide_group_rows(const GraphView<I>& g, uint32_
       T[v] = nt;
     }
     warp_append(keep, v, wl_out, cnt_out);
-    if (dsum != nullptr) warp_accumulate(lg == 0 ? len : 0, dsum);
+    dacc += lg == 0 ? len : 0;
   }
+  if (dsum != nullptr) warp_accumulate(dacc, dsum);
 }
 
 template <typename I, bool NC>

@@ -85,7 +85,8 @@ class mis2_stats(ctypes.Structure):
                 ("trace2", (ctypes.c_int64 * 4) * MIS2_TRACE_CAP),
                 ("kernel_ms", ctypes.c_double * MIS2_NUM_KERNEL_CLASSES),
                 ("kernel_launches", ctypes.c_int64 * MIS2_NUM_KERNEL_CLASSES),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64),
+                ("loop_ns", (ctypes.c_int64 * (4 + 4 * MIS2_TRACE_CAP)) * 2)]
 
 
 _LIB = None

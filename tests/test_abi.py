@@ -50,7 +50,7 @@ def test_struct_sizes_match_header():
     # int64 n, nnz; int32 x2; two pointers
     assert ctypes.sizeof(mis2.mis2_csr) == 40
     assert ctypes.sizeof(mis2.mis2_config) == 48
-    assert ctypes.sizeof(mis2.mis2_stats) == 4 + 4 + 8 * 4 + 2 * 64 * 4 * 8 + 8 * 8 + 8 * 8 + 8
+    assert ctypes.sizeof(mis2.mis2_stats) == 4 + 4 + 8 * 4 + 2 * 64 * 4 * 8 + 8 * 8 + 8 * 8 + 8 + 2 * (4 + 4 * 64) * 8
 
 
 def test_null_context_is_rejected(lib):
