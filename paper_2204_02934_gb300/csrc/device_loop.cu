@@ -84,7 +84,7 @@ struct LoopArgs {
 };
 
 template <int G, typename I>
-__global__ void __launch_bounds__(kBlock, 4) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
+__global__ void __launch_bounds__(kBlock, 2) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
   __shared__ uint32_t sh[40];
   __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
   int32_t* my_stage = stage[threadIdx.x >> 5];

@@ -110,27 +110,41 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
   const int lane = lane_id();
   WarpAppender app{stage_warp + kStageWarpWords, wl_out, cnt_out, 0};
   int64_t dacc = 0;
-  for (int64_t base = warp_begin * 32; base < n_in; base += warp_stride * 32) {
-    const int64_t i = base + lane;
-    const bool active = i < n_in;
-    int32_t v = 0;
-    int64_t s = 0, e = 0;
-    if (active) {
-      v = ld<false>(wl_in + i);
-      row_range(g, v, s, e);
-    }
+  // the next iteration's vertex and row bounds are loaded while this
+  // iteration's gathers are in flight
+  int64_t base = warp_begin * 32;
+  bool an = base + lane < n_in;
+  int32_t vn = 0;
+  int64_t sn = 0, en = 0;
+  if (an) {
+    vn = ld<false>(wl_in + base + lane);
+    row_range(g, vn, sn, en);
+  }
+  for (; base < n_in; base += warp_stride * 32) {
+    const bool active = an;
+    const int32_t v = vn;
+    const int64_t s = sn, e = en;
     const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
     const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
+    const int64_t inext = base + warp_stride * 32 + lane;
+    an = inext < n_in;
+    if (an) vn = ld<false>(wl_in + inext);
     uint32_t m = kOut;
     if (active) {
       m = ld<NC>(T + v);
       if (len >= 0) {
+        uint32_t t[kLaneRowMax];
 #pragma unroll
-        for (int k = 0; k < kLaneRowMax; k++)
-          if (k < len) m = min(m, ld<NC>(T + mine[k]));
+        for (int k = 0; k < kLaneRowMax; k++) t[k] = k < len ? ld<NC>(T + mine[k]) : kOut;
+        if (an) row_range(g, vn, sn, en);
+#pragma unroll
+        for (int k = 0; k < kLaneRowMax; k++) m = min(m, t[k]);
       } else {
+        if (an) row_range(g, vn, sn, en);
         visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) { m = min(m, ld<NC>(T + w)); });
       }
+    } else if (an) {
+      row_range(g, vn, sn, en);
     }
     bool keep = false;
     if (active) {
@@ -138,7 +152,7 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
       M[v] = m;
       keep = m != kOut;
     }
-    __syncwarp();  // slots are rewritten by the next iteration's copies
+    __syncwarp();  // staged rows are rewritten by the next iteration's copies
     app.push(keep, v);
     dacc += e - s;
   }
@@ -154,36 +168,44 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
   const int lane = lane_id();
   WarpAppender app{stage_warp + kStageWarpWords, wl_out, cnt_out, 0};
   int64_t dacc = 0;
-  for (int64_t base = warp_begin * 32; base < n_in; base += warp_stride * 32) {
-    const int64_t i = base + lane;
-    const bool active = i < n_in;
-    int32_t v = 0;
-    int64_t s = 0, e = 0;
-    if (active) {
-      v = ld<false>(wl_in + i);
-      row_range(g, v, s, e);
-    }
+  int64_t base = warp_begin * 32;
+  bool an = base + lane < n_in;
+  int32_t vn = 0;
+  int64_t sn = 0, en = 0;
+  if (an) {
+    vn = ld<false>(wl_in + base + lane);
+    row_range(g, vn, sn, en);
+  }
+  for (; base < n_in; base += warp_stride * 32) {
+    const bool active = an;
+    const int32_t v = vn;
+    const int64_t s = sn, e = en;
     const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
     const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
+    const int64_t inext = base + warp_stride * 32 + lane;
+    an = inext < n_in;
+    if (an) vn = ld<false>(wl_in + inext);
     bool keep = false;
     if (active) {
       const uint32_t t = ld<false>(T + v);
       const uint32_t mv = ld<NC>(M + v);
       bool any_out = mv == kOut, all_eq = mv == t;
       if (len >= 0) {
+        uint32_t mw[kLaneRowMax];
+#pragma unroll
+        for (int k = 0; k < kLaneRowMax; k++) mw[k] = k < len ? ld<NC>(M + mine[k]) : t;
+        if (an) row_range(g, vn, sn, en);
 #pragma unroll
         for (int k = 0; k < kLaneRowMax; k++) {
-          if (k < len) {
-            const uint32_t mw = ld<NC>(M + mine[k]);
-            any_out |= mw == kOut;
-            all_eq &= (mw == t) | (mw == 0u);
-          }
+          any_out |= mw[k] == kOut;
+          all_eq &= (mw[k] == t) | (mw[k] == 0u);
         }
       } else {
+        if (an) row_range(g, vn, sn, en);
         visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) {
-          const uint32_t mw = ld<NC>(M + w);
-          any_out |= mw == kOut;
-          all_eq &= (mw == t) | (mw == 0u);
+          const uint32_t x = ld<NC>(M + w);
+          any_out |= x == kOut;
+          all_eq &= (x == t) | (x == 0u);
         });
       }
       uint32_t nt;
@@ -196,6 +218,8 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
         keep = true;
       }
       T[v] = nt;
+    } else if (an) {
+      row_range(g, vn, sn, en);
     }
     __syncwarp();
     app.push(keep, v);
