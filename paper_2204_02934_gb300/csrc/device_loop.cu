@@ -12,6 +12,12 @@
 
 namespace mis2 {
 
+// Minimum resident blocks per SM the loop kernel is compiled for (register
+// budget: 65536 / (256 * MIS2_LOOP_MINB) per thread).
+#ifndef MIS2_LOOP_MINB
+#define MIS2_LOOP_MINB 2
+#endif
+
 constexpr int kErrTimeout = 1;
 constexpr int kErrNoProgress = 4;
 
@@ -84,7 +90,7 @@ struct LoopArgs {
 };
 
 template <int G, typename I>
-__global__ void __launch_bounds__(kBlock, 2) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
+__global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
   __shared__ uint32_t sh[40];
   __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
   int32_t* my_stage = stage[threadIdx.x >> 5];

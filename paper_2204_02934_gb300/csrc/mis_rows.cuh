@@ -154,7 +154,7 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
     }
     __syncwarp();  // staged rows are rewritten by the next iteration's copies
     app.push(keep, v);
-    dacc += e - s;
+    dacc += active ? e - s : 0;
   }
   app.flush();
   if (dsum != nullptr) warp_accumulate(dacc, dsum);
@@ -223,7 +223,7 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
     }
     __syncwarp();
     app.push(keep, v);
-    dacc += e - s;
+    dacc += active ? e - s : 0;
   }
   app.flush();
   if (dsum != nullptr) warp_accumulate(dacc, dsum);
