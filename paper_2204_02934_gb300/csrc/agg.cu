@@ -16,7 +16,6 @@
 
 namespace mis2 {
 
-constexpr int kErrNoAggregatedNeighbour = 2;
 constexpr int kPhase3Window = 8192;   // aggregate ids counted per pass for the heaviest rows
 constexpr int kPhase3SortCap = 8192;  // rows up to this length are sorted in shared memory
 
@@ -26,9 +25,11 @@ constexpr int kPhase3SortCap = 8192;  // rows up to this length are sorted in sh
 // degree >= block_degree are deferred to the block kernel.
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_agg_claim(GraphView<I> g, const int32_t* list, int64_t n_host,
-                                                      const int32_t* n_dev, int32_t* labels, int32_t base,
-                                                      int32_t* heavy, int32_t* heavy_cnt, int32_t block_degree) {
+                                                      const int32_t* n_dev, int32_t* labels, int32_t base_host,
+                                                      const int32_t* base_dev, int32_t* heavy, int32_t* heavy_cnt,
+                                                      int32_t block_degree) {
   const int64_t cnt = n_dev != nullptr ? *n_dev : n_host;
+  const int32_t base = base_dev != nullptr ? *base_dev : base_host;
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
@@ -50,8 +51,10 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim(GraphView<I> g, const int3
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_agg_claim_block(GraphView<I> g, const int32_t* list,
                                                             const int32_t* heavy, const int32_t* heavy_cnt,
-                                                            int32_t* labels, int32_t base) {
+                                                            int32_t* labels, int32_t base_host,
+                                                            const int32_t* base_dev) {
   const int64_t cnt = *heavy_cnt;
+  const int32_t base = base_dev != nullptr ? *base_dev : base_host;
   for (int64_t h = blockIdx.x; h < cnt; h += gridDim.x) {
     const int32_t j = heavy[h];
     const int32_t v = list[j];
@@ -347,15 +350,16 @@ static GraphView<I> gview(const GraphArgs& g) {
 
 template <typename I>
 static void launch_claim(mis2_ctx* c, const GraphView<I>& gv, const int32_t* list, int64_t n_host,
-                         const int32_t* n_dev, int32_t* labels, int32_t base, cudaStream_t st) {
+                         const int32_t* n_dev, int32_t* labels, int32_t base, cudaStream_t st,
+                         const int32_t* base_dev = nullptr) {
   Scratch& s = c->s;
   const int64_t items = n_dev != nullptr ? gv.n : n_host;
   cudaMemsetAsync(s.ctr + kCtrHeavy, 0, sizeof(int32_t), st);
   k_agg_claim<I><<<grid_for(c, items, kBlock / 32), kBlock, 0, st>>>(gv, list, n_host, n_dev, labels, base,
-                                                                      s.left_heavy, s.ctr + kCtrHeavy,
+                                                                      base_dev, s.left_heavy, s.ctr + kCtrHeavy,
                                                                       c->cfg.block_degree);
   k_agg_claim_block<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, list, s.left_heavy, s.ctr + kCtrHeavy, labels,
-                                                           base);
+                                                           base, base_dev);
   c->launches += 2;
 }
 
@@ -452,6 +456,52 @@ int agg_phase2(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* label
 
 int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, cudaStream_t st) {
   return g.rp64 ? phase3_t<int64_t>(c, g, labels, total, st) : phase3_t<int32_t>(c, g, labels, total, st);
+}
+
+template <typename I>
+static int agg_async_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const PrioCfg& p, int mode,
+                       int32_t* labels, cudaStream_t st) {
+  Scratch& s = c->s;
+  const GraphView<I> gv = gview<I>(g);
+  const int64_t n = g.n;
+  MIS2_CUDA(cudaMemsetAsync(labels, 0xFF, n * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrM2, 0, (kCtrLeftHeavy - kCtrM2 + 1) * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
+  timer_begin(c, kKcAggregate, st);
+  launch_claim<I>(c, gv, roots, 0, s.ctr + kCtrRoots, labels, 0, st);
+  timer_end(c, st);
+  if (mode == MIS2_AGG_ALG3) {
+    MIS2_TRY(mis2_rounds_device_async(c, g, labels, p, 1, kCtrRounds2, st));
+    MIS2_TRY(extract_in_set(c, n, nullptr, s.roots2, s.ctr + kCtrM2, st));
+    MIS2_CUDA(cudaMemsetAsync(s.qflag, 0, n, st));
+    timer_begin(c, kKcAggregate, st);
+    k_qualify<I><<<grid_for(c, n, kBlock / 32), kBlock, 0, st>>>(gv, s.roots2, s.ctr + kCtrM2, labels, s.qflag);
+    c->launches++;
+    timer_end(c, st);
+    MIS2_TRY(compact_flags(c, s.qflag, nullptr, n, s.qlist, s.ctr + kCtrQual, st));
+    timer_begin(c, kKcAggregate, st);
+    launch_claim<I>(c, gv, s.qlist, 0, s.ctr + kCtrQual, labels, 0, st, s.ctr + kCtrRoots);
+    timer_end(c, st);
+  }
+  timer_begin(c, kKcAggregate, st);
+  MIS2_CUDA(cudaMemcpyAsync(s.tent, labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  MIS2_CUDA(cudaMemsetAsync(s.aggsize, 0, n * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeft, 0, 2 * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
+  k_aggsize<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, s.tent, s.aggsize);
+  k_leftovers<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.left, s.ctr + kCtrLeft, s.left_mid,
+                                                             s.ctr + kCtrLeftMid, s.left_heavy, s.ctr + kCtrLeftHeavy);
+  c->launches += 2;
+  launch_phase3<I>(c, gv, labels, st);
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  return MIS2_OK;
+}
+
+int agg_level_async(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const PrioCfg& p, int mode, int32_t* labels,
+                    cudaStream_t st) {
+  return g.rp64 ? agg_async_t<int64_t>(c, g, roots, p, mode, labels, st)
+                : agg_async_t<int32_t>(c, g, roots, p, mode, labels, st);
 }
 
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed, int mode,

@@ -370,11 +370,69 @@ int mis2_coarsen(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t 
   return rc;
 }
 
+static int device_error(int32_t err) {
+  if (err & kErrTimeout) return MIS2_ERR_TIMEOUT;
+  if (err & kErrNoProgress) return MIS2_ERR_NO_PROGRESS;
+  if (err & kErrNoAggregatedNeighbour) return MIS2_ERR_BAD_GRAPH;
+  return MIS2_OK;
+}
+
+// One level with the persistent round loop and two host round trips: the
+// counts that size later steps (roots, phase-2 roots, large aggregates) stay
+// on the device and are read by the kernels that need them; the host waits
+// once for n_aggs (which sizes the coarse graph's launches) and once at the
+// end.  Results are those of the step-by-step path.
+static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* in_set, int32_t* rl, int32_t* lab,
+                      int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots, int64_t* n_aggs,
+                      int64_t* c_nnz, cudaStream_t st) {
+  Scratch& s = c->s;
+  const PrioCfg p = make_prio(c, ga.n, seed);
+  MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
+  MIS2_TRY(mis2_rounds_device_async(c, ga, nullptr, p, 0, kCtrRounds, st));
+  MIS2_TRY(extract_in_set(c, ga.n, in_set, rl, s.ctr + kCtrRoots, st));
+  MIS2_TRY(agg_level_async(c, ga, rl, p, c->cfg.agg_mode, lab, st));
+  MIS2_CUDA(cudaMemcpyAsync(c->h_trace, s.dtrace, 2 * MIS2_TRACE_CAP * 4 * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            st));
+  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MIS2_CUDA(cudaStreamSynchronize(st));
+  MIS2_TRY(device_error(c->h_ctr[kCtrErr]));
+  const int64_t nr = c->h_ctr[kCtrRoots];
+  const int64_t na = nr + c->h_ctr[kCtrQual];
+  c->stats.rounds = c->h_ctr[kCtrRounds];
+  c->stats.rounds2 = c->cfg.agg_mode == MIS2_AGG_ALG3 ? c->h_ctr[kCtrRounds2] : 0;
+  c->stats.n_roots = nr;
+  c->stats.n_phase1 = nr;
+  c->stats.n_aggs = na;
+  memcpy(c->stats.trace, c->h_trace, sizeof(c->stats.trace));
+  memset(c->stats.trace2, 0, sizeof(c->stats.trace2));
+  if (c->cfg.agg_mode == MIS2_AGG_ALG3)
+    memcpy(c->stats.trace2, c->h_trace + MIS2_TRACE_CAP * 4, sizeof(c->stats.trace2));
+  int64_t cn = 0;
+  if (c_rowptr != nullptr) {
+    MIS2_TRY(coarsen_fast(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, st));
+    MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MIS2_CUDA(cudaStreamSynchronize(st));
+    if (coarsen_fast_needs_retry(c)) {
+      MIS2_TRY(coarsen_impl(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, &cn, st));
+    } else {
+      if (c->h_ctr[kCtrErr] & kErrCapacity) return MIS2_ERR_INVALID_ARG;
+      cn = c->h_ctr[kCtrCnnz];
+    }
+    c->stats.c_nnz = cn;
+  }
+  if (n_roots) *n_roots = nr;
+  if (n_aggs) *n_aggs = na;
+  if (c_nnz) *c_nnz = cn;
+  return MIS2_OK;
+}
+
 static int level_impl(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* in_set, int32_t* roots,
                       int32_t* labels, int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                       int64_t* n_aggs, int64_t* c_nnz, cudaStream_t st) {
   int32_t* rl = roots != nullptr ? roots : c->s.roots_tmp;
   int32_t* lab = labels != nullptr ? labels : c->s.labels_tmp;
+  if (c->cfg.loop == MIS2_LOOP_DEVICE && ga.n > 0)
+    return level_fast(c, ga, seed, in_set, rl, lab, c_rowptr, c_colind, c_colind_cap, n_roots, n_aggs, c_nnz, st);
   int64_t nr = 0, na = 0, cn = 0;
   MIS2_TRY(run_impl(c, ga, make_prio(c, ga.n, seed), in_set, rl, &nr, nullptr, st));
   MIS2_TRY(aggregate_impl(c, ga, rl, nr, seed, c->cfg.agg_mode, lab, &na, st));

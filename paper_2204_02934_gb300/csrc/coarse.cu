@@ -217,9 +217,18 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
 // aggregate reads its bitmap out in order and clears it.
 
 // chunk_off[i] = number of 32-member chunks of the batch's aggregates < i.
+// With n_large_dev set (single-batch path), the batch is the first
+// min(kb, n_large) large aggregates, that count goes to *kb_out, and a larger
+// n_large raises kErrLargeOverflow.
 __global__ void k_large_chunks(const int32_t* large, int32_t k0, int32_t kb, const int32_t* agg_ptr,
-                               int64_t* chunk_off) {
+                               int64_t* chunk_off, const int32_t* n_large_dev, int32_t* kb_out, int32_t* err) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (n_large_dev != nullptr) {
+    const int32_t nl = *n_large_dev;
+    if (nl > kb) atomicOr(err, kErrLargeOverflow);
+    kb = min(kb, nl);
+    *kb_out = kb;
+  }
   int64_t acc = 0;
   for (int i = 0; i < kb; i++) {
     chunk_off[i] = acc;
@@ -233,8 +242,9 @@ template <typename I>
 __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32_t* labels, const int32_t* agg_ptr,
                                                      const int32_t* members, const int32_t* large, int32_t k0,
                                                      int32_t kb, const int64_t* chunk_off, uint32_t* bitmaps,
-                                                     int64_t words) {
+                                                     int64_t words, const int32_t* kb_dev) {
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
+  if (kb_dev != nullptr) kb = *kb_dev;
   const int64_t total = chunk_off[kb];
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < total; ch += nw) {
@@ -258,8 +268,9 @@ __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32
 
 __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int32_t k0, int32_t kb,
                                                        const int32_t* ub_ptr, uint32_t* bitmaps, int64_t words,
-                                                       int32_t* tmp, int32_t* c_cnt) {
+                                                       int32_t* tmp, int32_t* c_cnt, const int32_t* kb_dev) {
   __shared__ int sh[40];
+  if (kb_dev != nullptr) kb = *kb_dev;
   for (int i = blockIdx.x; i < kb; i += gridDim.x) {
     const int32_t a = large[k0 + i];
     uint32_t* bm = bitmaps + (int64_t)i * words;
@@ -282,11 +293,29 @@ __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int
   }
 }
 
+// Clears the bitmaps of a batch whose size is only known on the device.
+__global__ void __launch_bounds__(kBlock) k_large_zero(uint32_t* bitmaps, int64_t words, const int32_t* kb_dev) {
+  const int64_t total = (int64_t)*kb_dev * words;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    bitmaps[i] = 0u;
+}
+
+// Single-batch path: copies nothing when the large aggregates overflowed the
+// batch or the coarse rows exceed the output capacity (and flags the latter).
+__device__ __forceinline__ bool pack_refused(const int32_t* err, const int32_t* total, int64_t cap) {
+  if (err == nullptr) return false;
+  const bool over = *total > cap;
+  if (over && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(const_cast<int32_t*>(err), kErrCapacity);
+  return over || (*err & kErrLargeOverflow) != 0;
+}
+
 constexpr int kPackWarpMax = 4096;  // longer coarse rows are copied by the whole grid
 
 __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const int32_t* ub_ptr, const int32_t* c_cnt,
                                                         const int32_t* c_rowptr, const int32_t* tmp,
-                                                        int32_t* c_colind) {
+                                                        int32_t* c_colind, const int32_t* err, const int32_t* total,
+                                                        int64_t cap) {
+  if (pack_refused(err, total, cap)) return;
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
@@ -302,7 +331,9 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const in
 __global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* large, const int32_t* n_large,
                                                              const int32_t* ub_ptr, const int32_t* c_cnt,
                                                              const int32_t* c_rowptr, const int32_t* tmp,
-                                                             int32_t* c_colind) {
+                                                             int32_t* c_colind, const int32_t* err,
+                                                             const int32_t* total, int64_t cap) {
+  if (pack_refused(err, total, cap)) return;
   const int64_t nl = *n_large;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = 0; i < nl; i++) {
@@ -369,11 +400,11 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
     for (int32_t k0 = 0; k0 < n_large; k0 += slots) {
       const int32_t kb = std::min(slots, n_large - k0);
       MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)kb * words * sizeof(uint32_t), st));
-      k_large_chunks<<<1, 32, 0, st>>>(s.large, k0, kb, s.agg_ptr, s.chunk_off);
+      k_large_chunks<<<1, 32, 0, st>>>(s.large, k0, kb, s.agg_ptr, s.chunk_off, nullptr, nullptr, nullptr);
       k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, k0, kb,
-                                                        s.chunk_off, s.bitmaps, words);
+                                                        s.chunk_off, s.bitmaps, words, nullptr);
       k_large_emit<<<std::min<int32_t>(kb, c->sm_count * 2), kBlock, 0, st>>>(s.large, k0, kb, s.ub_ptr, s.bitmaps,
-                                                                             words, s.tmp, s.c_cnt);
+                                                                             words, s.tmp, s.c_cnt, nullptr);
       c->launches += 3;
     }
     timer_end(c, st);
@@ -386,11 +417,11 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   if (total > c_colind_cap) return MIS2_ERR_INVALID_ARG;
   timer_begin(c, kKcCoarse, st);
   k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
-                                                                        c_colind);
+                                                                        c_colind, nullptr, nullptr, 0);
   c->launches++;
   if (n_large > 0) {
     k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
-                                                           s.tmp, c_colind);
+                                                           s.tmp, c_colind, nullptr, nullptr, 0);
     c->launches++;
   }
   timer_end(c, st);
@@ -398,6 +429,80 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   *c_nnz = total;
   return MIS2_OK;
 }
+
+// The same coarse graph without a host round trip: the large aggregates go
+// through one bitmap batch sized on the host from n_aggs, whose count is read
+// on the device; the output capacity is checked on the device.  More large
+// aggregates than one batch holds set kErrLargeOverflow and the caller reruns
+// the batched path (coarsen_fast_needs_retry).
+template <typename I>
+static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
+                          int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st) {
+  Scratch& s = c->s;
+  GraphView<I> gv;
+  gv.rowptr = static_cast<const I*>(g.rowptr);
+  gv.colind = g.colind;
+  gv.n = g.n;
+  gv.nnz = g.nnz;
+  gv.vec = g.vec ? 1 : 0;
+  gv.pad = 0;
+  const int64_t n = g.n;
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCnnz, 0, sizeof(int32_t), st));
+  if (n_aggs == 0) {
+    MIS2_CUDA(cudaMemsetAsync(c_rowptr, 0, sizeof(int32_t), st));
+    return MIS2_OK;
+  }
+  timer_begin(c, kKcCoarse, st);
+  MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n_aggs * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n_aggs * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLarge, 0, 2 * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLargeKb, 0, sizeof(int32_t), st));
+  k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
+  c->launches++;
+  timer_end(c, st);
+  MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st));
+  MIS2_TRY(exclusive_scan_i32(c, s.ub, n_aggs, s.ub_ptr, nullptr, st));
+  timer_begin(c, kKcCoarse, st);
+  MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  k_coarse_scatter<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, labels, s.cursor, s.members);
+  const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
+  k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge);
+  const int64_t words = (n_aggs + 31) / 32;
+  const int64_t words_cap = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
+  const int32_t slots = (int32_t)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)coarse_bitmap_blocks(c) * words_cap / words, std::max<int64_t>(n_aggs, 1)));
+  k_large_chunks<<<1, 32, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
+                                   s.ctr + kCtrLargeKb, s.ctr + kCtrErr);
+  k_large_zero<<<c->sm_count * 2, kBlock, 0, st>>>(s.bitmaps, words, s.ctr + kCtrLargeKb);
+  k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, 0, slots,
+                                                    s.chunk_off, s.bitmaps, words, s.ctr + kCtrLargeKb);
+  k_large_emit<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, 0, slots, s.ub_ptr, s.bitmaps, words, s.tmp, s.c_cnt,
+                                                   s.ctr + kCtrLargeKb);
+  c->launches += 6;
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
+  timer_begin(c, kKcCoarse, st);
+  k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
+                                                                        c_colind, s.ctr + kCtrErr,
+                                                                        s.ctr + kCtrCnnz, c_colind_cap);
+  k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
+                                                         s.tmp, c_colind, s.ctr + kCtrErr, s.ctr + kCtrCnnz,
+                                                         c_colind_cap);
+  c->launches += 2;
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  return MIS2_OK;
+}
+
+int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
+                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st) {
+  return g.rp64 ? coarsen_fast_t<int64_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st)
+                : coarsen_fast_t<int32_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st);
+}
+
+bool coarsen_fast_needs_retry(const mis2_ctx* c) { return (c->h_ctr[kCtrErr] & kErrLargeOverflow) != 0; }
 
 int coarsen_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                  int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st) {

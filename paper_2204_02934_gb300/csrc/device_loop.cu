@@ -18,9 +18,6 @@ namespace mis2 {
 #define MIS2_LOOP_MINB 2
 #endif
 
-constexpr int kErrTimeout = 1;
-constexpr int kErrNoProgress = 4;
-
 __device__ __forceinline__ int ld_acquire_i32(const int32_t* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -86,7 +83,7 @@ struct LoopArgs {
   int32_t warp_degree;
   int32_t block_degree;
   int32_t max_rounds;
-  int32_t pad;
+  int32_t rounds_slot;
 };
 
 template <int G, typename I>
@@ -164,7 +161,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
                                   (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
     if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr)) return;
   }
-  if (tid == 0) ctr[kCtrRounds] = r;
+  if (tid == 0) ctr[a.rounds_slot] = r;
 }
 
 template <int G, typename I>
@@ -184,7 +181,7 @@ static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cud
 
 template <typename I>
 static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
-                           int trace_phase, cudaStream_t st, int32_t* rounds) {
+                           int trace_phase, cudaStream_t st, int32_t* rounds, bool sync, int rounds_slot) {
   Scratch& s = c->s;
   GraphView<I> gv;
   gv.rowptr = static_cast<const I*>(g.rowptr);
@@ -209,8 +206,15 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.warp_degree = c->cfg.warp_degree;
   la.block_degree = c->cfg.block_degree;
   la.max_rounds = (int32_t)std::min<int64_t>(g.n, (int64_t)1 << 30);
-  la.pad = 0;
-  MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
+  la.rounds_slot = rounds_slot;
+  if (sync) {
+    MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
+  } else {
+    // worklist counters and the barrier words only: other counters of the
+    // level (roots, errors) stay
+    MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, 18 * sizeof(int32_t), st));
+    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrBarrier, 0, 2 * sizeof(int32_t), st));
+  }
   MIS2_CUDA(cudaMemsetAsync(la.dtr, 0, MIS2_TRACE_CAP * 4 * sizeof(int64_t), st));
   timer_begin(c, kKcDeviceLoop, st);
   int rc;
@@ -224,23 +228,28 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   }
   timer_end(c, st);
   if (rc != MIS2_OK) return rc;
+  if (la.ts != nullptr)
+    MIS2_CUDA(cudaMemcpyAsync(c->stats.loop_ns[trace_phase], la.ts, kLoopTsWords * sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, st));
+  if (!sync) return MIS2_OK;
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MIS2_CUDA(cudaStreamSynchronize(st));
   if (c->h_ctr[kCtrErr] & kErrTimeout) return MIS2_ERR_TIMEOUT;
   if (c->h_ctr[kCtrErr] & kErrNoProgress) return MIS2_ERR_NO_PROGRESS;
-  *rounds = c->h_ctr[kCtrRounds];
-  if (la.ts != nullptr) {
-    MIS2_CUDA(cudaMemcpyAsync(c->stats.loop_ns[trace_phase], la.ts, kLoopTsWords * sizeof(int64_t),
-                              cudaMemcpyDeviceToHost, st));
-    MIS2_CUDA(cudaStreamSynchronize(st));
-  }
+  *rounds = c->h_ctr[rounds_slot];
   return MIS2_OK;
+}
+
+int mis2_rounds_device_async(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
+                             int trace_phase, int rounds_slot, cudaStream_t st) {
+  return g.rp64 ? rounds_device_t<int64_t>(c, g, labels, p, trace_phase, st, nullptr, false, rounds_slot)
+                : rounds_device_t<int32_t>(c, g, labels, p, trace_phase, st, nullptr, false, rounds_slot);
 }
 
 int mis2_rounds_device(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p, int trace_phase,
                        cudaStream_t st, int32_t* rounds) {
-  return g.rp64 ? rounds_device_t<int64_t>(c, g, labels, p, trace_phase, st, rounds)
-                : rounds_device_t<int32_t>(c, g, labels, p, trace_phase, st, rounds);
+  return g.rp64 ? rounds_device_t<int64_t>(c, g, labels, p, trace_phase, st, rounds, true, kCtrRounds)
+                : rounds_device_t<int32_t>(c, g, labels, p, trace_phase, st, rounds, true, kCtrRounds);
 }
 
 }  // namespace mis2

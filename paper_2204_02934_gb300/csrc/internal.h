@@ -30,9 +30,21 @@ enum : int {
   kCtrRounds = 27,   // rounds of the device loop
   kCtrBarrier = 28,  // grid barrier: arrive count (28), generation (29)
   kCtrLeftMid = 30,  // phase-3 leftovers of medium degree
+  kCtrRounds2 = 32,  // rounds of the phase-2 device loop
+  kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch
   kCtrWords = 64
 };
-constexpr int kReadbackWords = 32;
+constexpr int kReadbackWords = 40;
+// device error flags (ctr[kCtrErr])
+// kErrLargeOverflow: more large aggregates than one bitmap batch holds, seen
+// by the single-batch coarse path (the caller reruns the batched path).
+enum : int {
+  kErrTimeout = 1,
+  kErrNoAggregatedNeighbour = 2,
+  kErrNoProgress = 4,
+  kErrCapacity = 8,
+  kErrLargeOverflow = 16
+};
 constexpr int kLoopTsWords = MIS2_LOOP_TS_WORDS;
 
 enum KernelClass : int {
@@ -153,6 +165,10 @@ int mis2_rounds_host(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, con
 // Same through the persistent device-loop kernel.
 int mis2_rounds_device(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
                        int trace_phase, cudaStream_t st, int32_t* rounds);
+// Device loop without host synchronisation: rounds go to ctr[rounds_slot],
+// errors accumulate in ctr[kCtrErr] (cleared by the caller).
+int mis2_rounds_device_async(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
+                             int trace_phase, int rounds_slot, cudaStream_t st);
 // Ordered compaction of {v : T_v = IN}: ascending roots, flags, count on
 // device at ctr[kCtrRoots + which] (which: 0 roots, 1 phase-2 roots).
 int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32_t* count_dev,
@@ -172,6 +188,17 @@ int agg_phase1(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_
 int agg_phase2(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* labels, int32_t label_base,
                int32_t* rounds2, int64_t* nq, cudaStream_t st);
 int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, cudaStream_t st);
+// Sync-free variants: counts stay on the device (roots count at
+// ctr[kCtrRoots], qualifying phase-2 roots at ctr[kCtrQual]); errors in
+// ctr[kCtrErr].
+int agg_level_async(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const PrioCfg& p, int mode, int32_t* labels,
+                    cudaStream_t st);
+// Coarse graph without host synchronisation; the caller synchronises and
+// then checks coarsen_fast_needs_retry (more large aggregates than one batch
+// of bitmaps, or a c_colind too small) before trusting the result.
+int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
+                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st);
+bool coarsen_fast_needs_retry(const mis2_ctx* c);
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,
                    int mode, int32_t* labels, int64_t* n_aggs, cudaStream_t st);
 int coarsen_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,

@@ -72,6 +72,25 @@ def _graphs():
     yield "rmat12", gg.rmat(12, 8, seed=5)
     yield "rmat12_i32", gg.rmat(12, 8, seed=6, rowptr_dtype=np.int32)
     yield "elasticity5", gg.elasticity3d(5, 4, 3)
+    yield "grid_hubs", _grid_with_hubs()
+
+
+def _grid_with_hubs():
+    """A 120x120 grid plus three hubs tied to spread-out grid vertices: the
+    hubs' aggregates border hundreds of aggregates, so the coarse rows take
+    the large-aggregate (global bitmap) path."""
+    side = 120
+    base = gg.grid2d_5pt(side, side)
+    pairs = gg_pairs(base)
+    n = base.n + 3
+    extra = [(base.n + h, v) for h in range(3) for v in range(h * 7, base.n, 11)]
+    return gg.graph_from_edges(n, np.concatenate([pairs, np.array(extra, dtype=np.int64)]))
+
+
+def gg_pairs(g):
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr.astype(np.int64)))
+    keep = rows < g.colind
+    return np.stack([rows[keep], g.colind[keep].astype(np.int64)], axis=1)
 
 
 @pytest.mark.parametrize("loop", LOOPS)
@@ -204,6 +223,27 @@ def test_determinism_and_loop_drivers_agree():
     for o in outs[1:]:
         for k in ("labels", "c_colind", "roots"):
             assert np.array_equal(o[k], outs[0][k])
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_coarse_capacity_is_checked(loop):
+    """Too small a coarse colind buffer is refused (nothing written past it),
+    and the next call on the same context is unaffected."""
+    import torch
+
+    g = gg.grid3d_27pt(12, 11, 10)
+    ctx = make_ctx(g, loop=loop)
+    dg = mis2.DeviceGraph.from_host(g)
+    n = g.n
+    bufs = [torch.empty(n, dtype=t, device="cuda") for t in (torch.uint8, torch.int32, torch.int32)]
+    c_rowptr = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+    cap = 64
+    c_colind = torch.full((cap + 1024,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(mis2.Mis2Error) as e:
+        mis2.mis2_coarsen_level(ctx.handle, dg.csr, 0, *bufs, c_rowptr, c_colind, cap, None)
+    assert e.value.status == -1
+    assert bool((c_colind[cap:] == -7).all())
+    assert_level_equal(g, gpu_level(ctx, g, 0), seed=0)
 
 
 def test_invalid_arguments():
