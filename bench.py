@@ -6,7 +6,7 @@ MIS-2 (Algorithm 1), aggregation (Algorithm 3) and the coarse graph.  The
 metric is edges/s = input entries per step / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 27pt|small|rmat|batch]
+                  [--workload 27pt|small|rmat|serve]
 
 - value: device-resident input, CUDA events around each step, L2 flushed
   (256 MiB write) before every step, outside the timed interval.
@@ -404,6 +404,90 @@ def run_batch_compare(steps=3, warmup=2, n_graphs=512, seed=7, min_n=1000):
             "plain_ms": 1e3 * t_p, "batched_gpu_launches_per_step": launches // steps}
 
 
+def run_serve(args):
+    """Serving: a Poisson stream of one-level requests (H2D of the CSR, MIS-2,
+    aggregation, coarse graph, D2H of every output) drawn from a pool of 64
+    pinned-host graphs (3D 7-pt grids of side 20-160 and R-MAT graphs of scale
+    14-20, average degree 16).  Serial plain launches (one request at a time)
+    against continuous batching over `--slots` resident slots; p50/p99 latency
+    at the offered rate, saturation throughput with every request queued at
+    once, and the identity of each request's result alone and in the mix."""
+    from paper_2204_02934_gb300 import graphgen as gg
+
+    t_gen = time.perf_counter()
+    pool = gg.serving_pool(64, processes=max(1, min(16, os.cpu_count() or 1)))
+    t_gen = time.perf_counter() - t_gen
+    import torch
+
+    from paper_2204_02934_gb300 import _build, mis2
+
+    _build.build()
+    torch.cuda.init()
+    pins, host = [], []
+    for g in pool:
+        rp = torch.from_numpy(np.ascontiguousarray(g.rowptr)).pin_memory()
+        ci = torch.from_numpy(np.ascontiguousarray(g.colind)).pin_memory()
+        pins.append((rp, ci))
+        host.append(mis2.mis2_csr(g.n, g.nnz, 1 if rp.dtype == torch.int64 else 0, 0, rp.data_ptr(),
+                                  ci.data_ptr() if g.nnz else None))
+    max_n, max_nnz = max(g.n for g in pool), max(g.nnz for g in pool)
+    n_req, rate = args.requests, args.rate
+    arrivals = gg.poisson_arrivals(n_req, rate, seed=13)
+    idx = np.minimum((gg.uniform01(np.arange(n_req, dtype=np.uint64), 17) * len(pool)).astype(np.int32),
+                     len(pool) - 1)
+    n_sat = min(n_req, args.saturation_requests)
+
+    def summarize(res, t_first):
+        lat = np.array([r.t_done - r.t_arrive for r in res])
+        svc = np.array([r.t_done - r.t_start for r in res])
+        span = max(r.t_done for r in res) - t_first
+        return {"graphs_per_s": len(res) / span, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
+                "service_mean_ms": 1e3 * float(svc.mean())}
+
+    out, sums = {}, {}
+    for name, slots in (("serial", 1), ("continuous", args.slots)):
+        srv = mis2.Server(slots=slots, slot_max_n=max_n, slot_max_nnz=max_nnz, mem_budget=64 << 30,
+                          loop=mis2.MIS2_LOOP_DEVICE if args.loop == "device" else mis2.MIS2_LOOP_HOST)
+        srv.replay(host, np.zeros(len(pool)), np.arange(len(pool), dtype=np.int32), seed=0)  # warm-up
+        res, mif = srv.replay(host, arrivals, idx, seed=0)
+        if any(r.status != 0 for r in res):
+            raise SystemExit(f"serving: a request failed ({name})")
+        open_loop = summarize(res, min(r.t_arrive for r in res))
+        open_loop["max_in_flight"] = mif
+        sums[name] = [r.checksum for r in res]
+        res2, mif2 = srv.replay(host, np.zeros(n_sat), idx[:n_sat], seed=0)
+        sat = summarize(res2, min(r.t_arrive for r in res2))
+        sat["max_in_flight"] = mif2
+        sums[name + "_sat"] = [r.checksum for r in res2]
+        srv.close()
+        out[name] = {"slots": slots, "open_loop": open_loop, "saturation": sat}
+    same = sums["serial"] == sums["continuous"] and sums["serial_sat"] == sums["continuous_sat"]
+    per_graph = {}
+    for i, h in zip(idx, sums["serial"]):
+        per_graph.setdefault(int(i), set()).add(h)
+    same = same and all(len(v) == 1 for v in per_graph.values())
+    line = {
+        "metric": "serving graphs/s at saturation and p50/p99 latency at the offered rate (one coarsening level "
+                  "per request, H2D + compute + D2H)",
+        "value": round(out["continuous"]["saturation"]["graphs_per_s"], 1), "unit": "graphs/s",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"{n_req} requests, Poisson arrivals at {rate:g} req/s (seed 13), drawn uniformly "
+                               f"from 64 pinned-host graphs (3D 7-pt side log-uniform 20-160 / R-MAT scale 14-20, "
+                               f"avg degree 16, seed 11; {sum(g.nnz for g in pool)} entries in the pool); "
+                               f"saturation: {n_sat} requests queued at t=0",
+                   "slots": args.slots, "loop": args.loop},
+        "serial": out["serial"], "continuous": out["continuous"],
+        "speedup_vs_serial": {"saturation": out["continuous"]["saturation"]["graphs_per_s"] /
+                              out["serial"]["saturation"]["graphs_per_s"],
+                              "p99_at_offered_rate": out["serial"]["open_loop"]["p99_ms"] /
+                              out["continuous"]["open_loop"]["p99_ms"]},
+        "identical_output": bool(same), "pool_generation_s": round(t_gen, 1),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _traffic_from_profile(kernel):
     """dram bytes per launch recorded by an ncu capture of this kernel, when
     the recorded source digest still matches the library sources."""
@@ -431,12 +515,18 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat"])
+    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat", "serve"])
     ap.add_argument("--loop", default="device", choices=["device", "host"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--requests", type=int, default=20000, help="serve: requests in the Poisson stream")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
+    ap.add_argument("--slots", type=int, default=4, help="serve: continuous-batching slots")
+    ap.add_argument("--saturation-requests", type=int, default=4000)
     args = ap.parse_args()
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

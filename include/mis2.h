@@ -276,14 +276,23 @@ typedef struct {
   int64_t mem_budget;     /* bytes of request buffers admitted at once (default 8 GiB) */
   int64_t slot_max_n;     /* largest request per slot (vertices, entries) */
   int64_t slot_max_nnz;
-  mis2_config cfg;        /* per-slot configuration (default loop: MIS2_LOOP_HOST) */
+  mis2_config cfg;        /* per-slot configuration (default loop: MIS2_LOOP_DEVICE; the slots
+                             share a lock so that one device-loop kernel runs at a time, the
+                             other steps of their requests overlap freely) */
 } mis2_server_config;
 
 typedef struct {
   int64_t ticket;
   int64_t n, nnz;
   int64_t n_roots, n_aggs, c_nnz;
-  uint64_t checksum;        /* FNV-1a over roots, labels, coarse rowptr and colind */
+  /* Fingerprint of the outputs, computed on the device: with
+   * mix(z) = the SplitMix64 finaliser (z ^= z>>30; z *= 0xBF58476D1CE4E5B9;
+   * z ^= z>>27; z *= 0x94D049BB133111EB; z ^= z>>31), arrays A_0..A_3 =
+   * roots[n_roots], labels[n], c_rowptr[n_aggs+1], c_colind[c_nnz] and
+   * counts (n_roots, n_aggs, c_nnz), it is the sum mod 2^64 of
+   * mix(mix((k << 40) + i) ^ (uint32)A_k[i]) over every k, i, plus
+   * mix(((uint64)(5 + j) << 40) ^ count_j) for j = 0..2. */
+  uint64_t checksum;
   double t_arrive, t_start, t_done;  /* seconds since the server was created */
   int32_t status;           /* mis2_status of the request */
   int32_t slot;

@@ -73,6 +73,20 @@ __global__ void __launch_bounds__(kBlock) k_coarse_scatter(int64_t n, const int3
   }
 }
 
+// Labels of a staged row (W unrolled gathers, len <= W): -1 where absent or
+// equal to a.
+template <int W, typename FB>
+__device__ __forceinline__ void staged_labels(const int32_t* labels, const int32_t* row, int len, int32_t a,
+                                              FB&& fb) {
+  int32_t lab[W];
+#pragma unroll
+  for (int j = 0; j < W; j++) {
+    const int32_t l = j < len ? labels[row[j]] : a;
+    lab[j] = l != a ? l : -1;
+  }
+  fb(lab);
+}
+
 // Walk every fine entry of aggregate a (members [mb, me)) with one warp.
 // fb(lab) receives a register array of neighbour labels, -1 where the entry
 // is absent or belongs to a itself; every lane calls it with its own array
@@ -88,15 +102,12 @@ __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int3
     const bool has = k < me;
     if (has) row_range(g, members[k], s, e);
     const int len = has && e - s <= kLaneRowMax ? (int)(e - s) : -1;
-    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
+    int wd;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp, &wd);
     if (len > 0) {
-      int32_t lab[kLaneRowMax];
-#pragma unroll
-      for (int j = 0; j < kLaneRowMax; j++) {
-        const int32_t l = j < len ? labels[mine[j]] : a;
-        lab[j] = l != a ? l : -1;
-      }
-      fb(lab);
+      if (wd == 8) staged_labels<8>(labels, mine, len, a, fb);
+      else if (wd == 16) staged_labels<16>(labels, mine, len, a, fb);
+      else staged_labels<32>(labels, mine, len, a, fb);
     }
     __syncwarp();
     unsigned longm = __ballot_sync(kFull, has && len < 0);
@@ -125,6 +136,182 @@ __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int3
   }
 }
 
+// Small aggregates (at most kSmallMembers members and kSmallEntries fine
+// entries) are handled several at a time by one warp, without a hash set:
+// a warp takes kSmallWindow consecutive aggregate ids, groups its small
+// aggregates into
+// sub-batches of at most 32 members and 256 entries, loads every entry of a
+// sub-batch at once (8 per lane), forms keys (local aggregate << 27 | label)
+// for labels of other aggregates, sorts the 256 keys in registers (bitonic),
+// and writes each aggregate's distinct labels in ascending order.  The keys
+// need n_aggs < 2^27; larger aggregations take the hash path throughout.
+constexpr int kSmallMembers = 32;
+constexpr int kSmallK = 8;  // keys per lane
+constexpr int kSmallEntries = 32 * kSmallK;
+constexpr int kSmallLabelBits = 27;
+constexpr int kSmallWindow = 8;  // aggregate ids per warp task
+
+__device__ __forceinline__ bool small_aggregate(int32_t members, int32_t ub, bool enabled) {
+  return enabled && members <= kSmallMembers && ub <= kSmallEntries;
+}
+
+__device__ __forceinline__ int warp_inclusive_sum(int x) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Ascending bitonic sort of 32 * kSmallK keys held lane-major (key index =
+// lane * kSmallK + r).
+__device__ __forceinline__ void warp_sort_keys(uint32_t (&k)[kSmallK]) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int size = 2; size <= kSmallEntries; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride < kSmallK) {
+#pragma unroll
+        for (int r = 0; r < kSmallK; r++) {
+          const int q = r ^ stride;
+          if (q > r) {
+            const bool up = (((lane * kSmallK + r) & size) == 0);
+            const uint32_t x = k[r], y = k[q];
+            const bool sw = (x > y) == up;
+            k[r] = sw ? y : x;
+            k[q] = sw ? x : y;
+          }
+        }
+      } else {
+        const int lx = stride / kSmallK;
+        const bool lower = (lane & lx) == 0;
+#pragma unroll
+        for (int r = 0; r < kSmallK; r++) {
+          const uint32_t o = __shfl_xor_sync(kFull, k[r], lx);
+          const bool up = (((lane * kSmallK + r) & size) == 0);
+          k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
+        }
+      }
+    }
+  }
+}
+
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const int32_t* labels, int64_t n_aggs,
+                                                         const int32_t* agg_ptr, const int32_t* members,
+                                                         const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp,
+                                                         int32_t* c_cnt) {
+  __shared__ int32_t sh_cnt[kBlock / 32][32];
+  __shared__ int32_t sh_sel[kBlock / 32][32];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  int32_t* cnt = sh_cnt[wib];  // distinct labels per local aggregate
+  int32_t* sel = sh_sel[wib];  // local aggregate -> lane of its id in the window
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t A = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kSmallWindow; A < n_aggs;
+       A += nw * kSmallWindow) {
+    const int64_t a = A + lane;
+    const bool in = lane < kSmallWindow && a < n_aggs;
+    const int32_t p0 = in ? agg_ptr[a] : 0;
+    const int32_t p1 = in ? agg_ptr[a + 1] : 0;
+    const int32_t u = in ? ub[a] : 0;
+    const bool sm = in && small_aggregate(p1 - p0, u, true);
+    const int32_t outb = sm ? ub_ptr[a] : 0;
+    const int m = sm ? p1 - p0 : 0;
+    const int um = sm ? u : 0;
+    const int cm = warp_inclusive_sum(m);
+    const int cu = warp_inclusive_sum(um);
+    unsigned smask = __ballot_sync(kFull, sm);
+    while (smask) {
+      // sub-batch: the remaining small lanes in order while the members stay
+      // <= 32 and the entries <= 256 (the first one always fits)
+      const int i0 = __ffs(smask) - 1;
+      const int bm0 = __shfl_sync(kFull, cm - m, i0);
+      const int bu0 = __shfl_sync(kFull, cu - um, i0);
+      const unsigned bm = __ballot_sync(kFull, ((smask >> lane) & 1u) && cm - bm0 <= kSmallMembers &&
+                                                   cu - bu0 <= kSmallEntries);
+      smask &= ~bm;
+      const bool mine = (bm >> lane) & 1u;
+      const int slot0 = cm - m - bm0;  // first member slot of this lane's aggregate
+      if (mine) {
+        const int li = __popc(bm & ((1u << lane) - 1u));
+        sel[li] = lane;
+        cnt[li] = 0;
+      }
+      const unsigned starts = __reduce_or_sync(kFull, mine ? 1u << slot0 : 0u);
+      const int M = __shfl_sync(kFull, cm, 31 - __clz(bm)) - bm0;
+      __syncwarp();
+      // member slot `lane`: its local aggregate, owner lane, vertex, row
+      const int loc = lane < M ? __popc(starts & ((2u << lane) - 1u)) - 1 : 0;
+      const int owner = sel[loc];
+      const int32_t own_p0 = __shfl_sync(kFull, p0, owner);
+      const int own_slot0 = __shfl_sync(kFull, slot0, owner);
+      int64_t s = 0, e = 0;
+      if (lane < M) row_range(g, members[own_p0 + (lane - own_slot0)], s, e);
+      const int d = (int)(e - s);
+      const int offi = warp_inclusive_sum(d);
+      const int E = __shfl_sync(kFull, offi, 31);
+      const int offx = offi - d;
+      // entry t = r * 32 + lane: its member (last slot with offx <= t), column, label
+      int32_t w[kSmallK];
+      int lj[kSmallK];
+#pragma unroll
+      for (int r = 0; r < kSmallK; r++) {
+        const int t = r * 32 + lane;
+        int lo = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          const int c = lo + step;
+          const int oc = __shfl_sync(kFull, offx, c & 31);
+          if (c < M && oc <= t) lo = c;
+        }
+        const int64_t sj = __shfl_sync(kFull, s, lo);
+        const int oj = __shfl_sync(kFull, offx, lo);
+        lj[r] = __shfl_sync(kFull, loc, lo);
+        w[r] = t < E ? g.colind[sj + (t - oj)] : -1;
+      }
+      uint32_t key[kSmallK];
+#pragma unroll
+      for (int r = 0; r < kSmallK; r++) {
+        const int32_t l = w[r] >= 0 ? labels[w[r]] : -1;
+        const int32_t own = (int32_t)A + sel[lj[r]];
+        key[r] = (l >= 0 && l != own) ? ((uint32_t)lj[r] << kSmallLabelBits) | (uint32_t)l : 0xFFFFFFFFu;
+      }
+      warp_sort_keys(key);
+      // distinct keys in order: their index among all distinct keys
+      uint32_t prev = __shfl_up_sync(kFull, key[kSmallK - 1], 1);
+      if (lane == 0) prev = 0xFFFFFFFFu;
+      bool uq[kSmallK];
+      int nu = 0;
+#pragma unroll
+      for (int r = 0; r < kSmallK; r++) {
+        uq[r] = key[r] != 0xFFFFFFFFu && key[r] != (r == 0 ? prev : key[r - 1]);
+        nu += uq[r] ? 1 : 0;
+        if (uq[r]) atomicAdd(cnt + (key[r] >> kSmallLabelBits), 1);
+      }
+      const int ubase = warp_inclusive_sum(nu) - nu;
+      __syncwarp();
+      const int nb = __popc(bm);
+      const int cl = lane < nb ? cnt[lane] : 0;
+      const int first_u = warp_inclusive_sum(cl) - cl;  // first distinct index of local aggregate `lane`
+      const int out_l = __shfl_sync(kFull, outb, lane < nb ? sel[lane] : 0);  // ub_ptr of local aggregate `lane`
+      if (lane < nb) c_cnt[A + sel[lane]] = cl;
+      int ui = ubase;
+#pragma unroll
+      for (int r = 0; r < kSmallK; r++) {
+        const int l = uq[r] ? (int)(key[r] >> kSmallLabelBits) : 0;
+        const int fu = __shfl_sync(kFull, first_u, l);
+        const int ob = __shfl_sync(kFull, out_l, l);
+        if (uq[r]) tmp[ob + (ui - fu)] = (int32_t)(key[r] & ((1u << kSmallLabelBits) - 1u));
+        ui += uq[r] ? 1 : 0;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // Warp per aggregate: insert every neighbour label into a shared-memory hash
 // set (256 slots, linear probing); first insertions form the distinct list,
 // which is then sorted (bitonic, a few dozen entries) and written out.  An
@@ -139,7 +326,8 @@ __device__ __forceinline__ uint32_t label_hash(int32_t l) { return ((uint32_t)l 
 template <typename I>
 __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
     GraphView<I> g, const int32_t* labels, int64_t n_aggs, const int32_t* agg_ptr, const int32_t* members,
-    const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt, int32_t* large, int32_t* large_cnt) {
+    const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt, int32_t* large, int32_t* large_cnt,
+    bool small_on) {
   __shared__ int32_t sbuf[kCoarseWarps][kSortCap];
   __shared__ __align__(16) int32_t stage[kCoarseWarps][kStageWarpWords];
   __shared__ int32_t scnt[kCoarseWarps];
@@ -148,7 +336,9 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
   int32_t* dl = sbuf[wib] + kHashSlots;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
-    if (ub[a] > kWarpEntries) {
+    const int32_t ua = ub[a];
+    if (small_aggregate(agg_ptr[a + 1] - agg_ptr[a], ua, small_on)) continue;  // k_coarse_small's
+    if (ua > kWarpEntries) {
       if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
       continue;
     }
@@ -382,9 +572,17 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   timer_begin(c, kKcCoarse, st);
   MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   k_coarse_scatter<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, labels, s.cursor, s.members);
+  // the batched path pays off when small aggregates are common: average
+  // entries per aggregate at most half the sub-batch
+  const bool small_on = n_aggs < ((int64_t)1 << kSmallLabelBits) && g.nnz <= (int64_t)(kSmallEntries / 2) * n_aggs;
+  if (small_on) {
+    k_coarse_small<I><<<grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, 0, st>>>(
+        gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
+    c->launches++;
+  }
   const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
   k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
-                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge);
+                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on);
   c->launches += 2;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
@@ -465,9 +663,17 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   timer_begin(c, kKcCoarse, st);
   MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   k_coarse_scatter<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, labels, s.cursor, s.members);
+  // the batched path pays off when small aggregates are common: average
+  // entries per aggregate at most half the sub-batch
+  const bool small_on = n_aggs < ((int64_t)1 << kSmallLabelBits) && g.nnz <= (int64_t)(kSmallEntries / 2) * n_aggs;
+  if (small_on) {
+    k_coarse_small<I><<<grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, 0, st>>>(
+        gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
+    c->launches++;
+  }
   const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
   k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
-                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge);
+                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on);
   const int64_t words = (n_aggs + 31) / 32;
   const int64_t words_cap = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
   const int32_t slots = (int32_t)std::max<int64_t>(

@@ -174,7 +174,14 @@ static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cud
   const int blocks = c->sm_count * std::min(per_sm, want);
   c->device_loop_blocks = blocks;
   void* args[] = {&gv, &p, &la};
-  MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+  if (c->coop_lock != nullptr) {
+    std::lock_guard<std::mutex> lk(*c->coop_lock);
+    MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+    MIS2_CUDA(cudaEventRecord(c->coop_done, st));
+    MIS2_CUDA(cudaEventSynchronize(c->coop_done));
+  } else {
+    MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+  }
   c->launches++;
   return MIS2_OK;
 }

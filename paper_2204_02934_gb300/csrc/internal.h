@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -123,6 +124,11 @@ struct mis2_ctx {
   std::vector<void*> allocations;
   int device_loop_blocks = 0;  // co-resident blocks of the device-loop kernel
   int64_t launches = 0;        // kernels launched by the current call
+  // Contexts whose streams run concurrently (server slots) share this lock:
+  // a device-loop launch holds it until the kernel has finished, so at most
+  // one grid-synchronised kernel of theirs is resident at a time.
+  std::mutex* coop_lock = nullptr;
+  cudaEvent_t coop_done = nullptr;
 };
 
 namespace mis2 {

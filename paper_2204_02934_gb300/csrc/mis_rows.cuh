@@ -72,12 +72,18 @@ struct WarpAppender {
 // starts there.  When the 32 rows are back to back in colind (worklists that
 // still hold runs of consecutive vertices), the whole span moves with 16-byte
 // copies, 512 contiguous bytes per instruction; otherwise each row moves with
-// one coalesced 4-byte copy per entry, into padded per-lane slots.  Every
-// lane of the warp must call this; on return every staged row is visible to
-// its lane.  `nnz` bounds the 16-byte copies to the colind allocation.
+// one coalesced 4-byte copy per entry, into padded per-lane slots (4 rows
+// per copy instruction when no row is longer than 8, 2 when none is longer
+// than 16).  Every lane of the warp must call this; on return every staged
+// row is visible to its lane, and *width (when given) holds 8, 16 or 32: the
+// smallest of them bounding every staged row of the warp.  `nnz` bounds the
+// 16-byte copies to the colind allocation.
 __device__ __forceinline__ const int32_t* stage_rows_warp(const int32_t* __restrict__ colind, int64_t nnz, bool vec,
-                                                          int64_t s, int len, int32_t* area) {
+                                                          int64_t s, int len, int32_t* area, int* width = nullptr) {
   const int lane = lane_id();
+  const int ml = (int)__reduce_max_sync(kFull, (unsigned)(len > 0 ? len : 0));
+  const int wd = ml <= 8 ? 8 : (ml <= 16 ? 16 : 32);
+  if (width != nullptr) *width = wd;
   const int64_t s_next = __shfl_down_sync(kFull, s, 1);
   const int64_t e = s + (len > 0 ? len : 0);
   const bool joined = lane == 31 || e == s_next;
@@ -91,15 +97,63 @@ __device__ __forceinline__ const int32_t* stage_rows_warp(const int32_t* __restr
     __syncwarp();
     return area + (s - a);
   }
+  if (wd == 8) {
+#pragma unroll
+    for (int j0 = 0; j0 < 32; j0 += 4) {
+      const int j = j0 + (lane >> 3), c = lane & 7;
+      const int64_t sj = __shfl_sync(kFull, s, j);
+      const int lj = __shfl_sync(kFull, len, j);
+      if (c < lj) cp_async4(area + j * kRowSlot + c, colind + sj + c);
+    }
+  } else if (wd == 16) {
 #pragma unroll 4
-  for (int j = 0; j < 32; j++) {
-    const int64_t sj = __shfl_sync(kFull, s, j);
-    const int lj = __shfl_sync(kFull, len, j);
-    if (lane < lj) cp_async4(area + j * kRowSlot + lane, colind + sj + lane);
+    for (int j0 = 0; j0 < 32; j0 += 2) {
+      const int j = j0 + (lane >> 4), c = lane & 15;
+      const int64_t sj = __shfl_sync(kFull, s, j);
+      const int lj = __shfl_sync(kFull, len, j);
+      if (c < lj) cp_async4(area + j * kRowSlot + c, colind + sj + c);
+    }
+  } else {
+#pragma unroll 4
+    for (int j = 0; j < 32; j++) {
+      const int64_t sj = __shfl_sync(kFull, s, j);
+      const int lj = __shfl_sync(kFull, len, j);
+      if (lane < lj) cp_async4(area + j * kRowSlot + lane, colind + sj + lane);
+    }
   }
   cp_async_wait_all();
   __syncwarp();
   return area + lane * kRowSlot;
+}
+
+// min(m, T[row[k]] for k < len) with W unrolled gathers (len <= W); between()
+// runs after the gathers are issued, before their values are used.
+template <int W, bool NC, typename F>
+__device__ __forceinline__ uint32_t gather_min(const uint32_t* T, const int32_t* row, int len, uint32_t m,
+                                               F&& between) {
+  uint32_t t[W];
+#pragma unroll
+  for (int k = 0; k < W; k++) t[k] = k < len ? ld<NC>(T + row[k]) : kOut;
+  between();
+#pragma unroll
+  for (int k = 0; k < W; k++) m = min(m, t[k]);
+  return m;
+}
+
+// The decide tests over M[row[k]], k < len (len <= W): any OUT, all equal to
+// t or 0 (masked neighbours of a phase-2 MIS-2).
+template <int W, bool NC, typename F>
+__device__ __forceinline__ void gather_decide(const uint32_t* M, const int32_t* row, int len, uint32_t t,
+                                              bool& any_out, bool& all_eq, F&& between) {
+  uint32_t mw[W];
+#pragma unroll
+  for (int k = 0; k < W; k++) mw[k] = k < len ? ld<NC>(M + row[k]) : t;
+  between();
+#pragma unroll
+  for (int k = 0; k < W; k++) {
+    any_out |= mw[k] == kOut;
+    all_eq &= (mw[k] == t) | (mw[k] == 0u);
+  }
 }
 
 template <typename I, bool NC>
@@ -125,7 +179,8 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
     const int32_t v = vn;
     const int64_t s = sn, e = en;
     const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
-    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
+    int wd;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp, &wd);
     const int64_t inext = base + warp_stride * 32 + lane;
     an = inext < n_in;
     if (an) vn = ld<false>(wl_in + inext);
@@ -133,12 +188,12 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
     if (active) {
       m = ld<NC>(T + v);
       if (len >= 0) {
-        uint32_t t[kLaneRowMax];
-#pragma unroll
-        for (int k = 0; k < kLaneRowMax; k++) t[k] = k < len ? ld<NC>(T + mine[k]) : kOut;
-        if (an) row_range(g, vn, sn, en);
-#pragma unroll
-        for (int k = 0; k < kLaneRowMax; k++) m = min(m, t[k]);
+        auto nb = [&]() {
+          if (an) row_range(g, vn, sn, en);
+        };
+        if (wd == 8) m = gather_min<8, NC>(T, mine, len, m, nb);
+        else if (wd == 16) m = gather_min<16, NC>(T, mine, len, m, nb);
+        else m = gather_min<32, NC>(T, mine, len, m, nb);
       } else {
         if (an) row_range(g, vn, sn, en);
         visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) { m = min(m, ld<NC>(T + w)); });
@@ -181,7 +236,8 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
     const int32_t v = vn;
     const int64_t s = sn, e = en;
     const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
-    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp);
+    int wd;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp, &wd);
     const int64_t inext = base + warp_stride * 32 + lane;
     an = inext < n_in;
     if (an) vn = ld<false>(wl_in + inext);
@@ -191,15 +247,12 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
       const uint32_t mv = ld<NC>(M + v);
       bool any_out = mv == kOut, all_eq = mv == t;
       if (len >= 0) {
-        uint32_t mw[kLaneRowMax];
-#pragma unroll
-        for (int k = 0; k < kLaneRowMax; k++) mw[k] = k < len ? ld<NC>(M + mine[k]) : t;
-        if (an) row_range(g, vn, sn, en);
-#pragma unroll
-        for (int k = 0; k < kLaneRowMax; k++) {
-          any_out |= mw[k] == kOut;
-          all_eq &= (mw[k] == t) | (mw[k] == 0u);
-        }
+        auto nb = [&]() {
+          if (an) row_range(g, vn, sn, en);
+        };
+        if (wd == 8) gather_decide<8, NC>(M, mine, len, t, any_out, all_eq, nb);
+        else if (wd == 16) gather_decide<16, NC>(M, mine, len, t, any_out, all_eq, nb);
+        else gather_decide<32, NC>(M, mine, len, t, any_out, all_eq, nb);
       } else {
         if (an) row_range(g, vn, sn, en);
         visit_row<1>(g.colind, g.nnz, s, e, 0, g.vec, [&](int32_t w) {

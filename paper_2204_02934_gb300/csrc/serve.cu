@@ -21,13 +21,25 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
-  const unsigned char* c = static_cast<const unsigned char*>(p);
-  for (size_t i = 0; i < bytes; i++) {
-    h ^= c[i];
-    h *= 1099511628211ull;
-  }
-  return h;
+// SplitMix64 finaliser (Steele, Lea and Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Adds sum_i mix(mix((k << 40) + i) ^ (uint32)a[i]) to *out (mod 2^64): a
+// position-dependent fingerprint whose value does not depend on the order in
+// which the terms are added.
+__global__ void k_fingerprint(const int32_t* a, int64_t n, uint64_t k, unsigned long long* out) {
+  uint64_t acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += mix64(mix64((k << 40) + (uint64_t)i) ^ (uint64_t)(uint32_t)a[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc != 0) atomicAdd(out, (unsigned long long)acc);
 }
 
 struct Request {
@@ -44,6 +56,8 @@ struct Slot {
   uint8_t* in_set = nullptr;  // pinned host outputs
   int32_t *roots = nullptr, *labels = nullptr, *c_rowptr = nullptr, *c_colind = nullptr;
   int64_t cap_cci = 0;
+  unsigned long long* d_sum = nullptr;  // device fingerprint accumulator
+  unsigned long long* h_sum = nullptr;  // pinned landing
 };
 
 }  // namespace
@@ -62,6 +76,7 @@ struct mis2_server {
   int64_t max_in_flight = 0, in_flight = 0;
   bool stop = false;
   int device = 0;
+  std::mutex coop_mu;  // one device-loop kernel of the slots at a time
   Clock::time_point t0;
 };
 
@@ -76,6 +91,28 @@ int64_t request_bytes(const mis2_csr& g) {
 
 double secs(const mis2_server* s, Clock::time_point t) {
   return std::chrono::duration<double>(t - s->t0).count();
+}
+
+// Fingerprint of the slot's last results (the device copies the host-buffer
+// entry point left in the context's stage).
+int fingerprint(mis2_ctx* c, Slot& sl, int64_t n, int64_t nr, int64_t na, int64_t cn, uint64_t* out) {
+  const mis2::HostStage& h = c->stage;
+  MIS2_CUDA(cudaMemsetAsync(sl.d_sum, 0, sizeof(unsigned long long), sl.stream));
+  const int32_t* arr[4] = {h.roots, h.labels, h.c_rowptr, h.c_colind};
+  const int64_t len[4] = {nr, n, na + 1, cn};
+  for (int k = 0; k < 4; k++) {
+    if (len[k] <= 0) continue;
+    const int blocks = (int)std::min<int64_t>((len[k] + 255) / 256, (int64_t)c->sm_count * 4);
+    k_fingerprint<<<blocks, 256, 0, sl.stream>>>(arr[k], len[k], (uint64_t)k, sl.d_sum);
+  }
+  MIS2_CUDA(cudaGetLastError());
+  MIS2_CUDA(cudaMemcpyAsync(sl.h_sum, sl.d_sum, sizeof(unsigned long long), cudaMemcpyDeviceToHost, sl.stream));
+  MIS2_CUDA(cudaStreamSynchronize(sl.stream));
+  uint64_t f = *sl.h_sum;
+  const int64_t cnt[3] = {nr, na, cn};
+  for (int j = 0; j < 3; j++) f += mix64(((uint64_t)(5 + j) << 40) ^ (uint64_t)cnt[j]);
+  *out = f;
+  return MIS2_OK;
 }
 
 void worker_main(mis2_server* s, int slot_id) {
@@ -112,12 +149,7 @@ void worker_main(mis2_server* s, int slot_id) {
       res.n_roots = nr;
       res.n_aggs = na;
       res.c_nnz = cn;
-      uint64_t h = 1469598103934665603ull;
-      h = fnv1a(h, sl.roots, (size_t)nr * 4);
-      h = fnv1a(h, sl.labels, (size_t)rq.g.n * 4);
-      h = fnv1a(h, sl.c_rowptr, (size_t)(na + 1) * 4);
-      h = fnv1a(h, sl.c_colind, (size_t)cn * 4);
-      res.checksum = h;
+      res.status = fingerprint(sl.ctx, sl, rq.g.n, nr, na, cn, &res.checksum);
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
@@ -145,7 +177,7 @@ void mis2_server_config_default(mis2_server_config* c) {
   c->slot_max_n = (int64_t)1 << 22;
   c->slot_max_nnz = (int64_t)1 << 25;
   mis2_config_default(&c->cfg);
-  c->cfg.loop = MIS2_LOOP_HOST;
+  c->cfg.loop = MIS2_LOOP_DEVICE;
 }
 
 int mis2_server_create(mis2_server** out, const mis2_server_config* cfg) {
@@ -163,6 +195,9 @@ int mis2_server_create(mis2_server** out, const mis2_server_config* cfg) {
     int rc = mis2_ctx_create(&sl.ctx, cfg->slot_max_n, cfg->slot_max_nnz, &cfg->cfg);
     if (rc == MIS2_OK && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
       rc = MIS2_ERR_CUDA;
+    if (rc == MIS2_OK && cudaEventCreateWithFlags(&sl.ctx->coop_done, cudaEventDisableTiming) != cudaSuccess)
+      rc = MIS2_ERR_CUDA;
+    if (rc == MIS2_OK) sl.ctx->coop_lock = &s->coop_mu;
     if (rc != MIS2_OK) {
       mis2_server_destroy(s);
       return rc;
@@ -171,7 +206,8 @@ int mis2_server_create(mis2_server** out, const mis2_server_config* cfg) {
     sl.cap_cci = nnz;
     if (cudaMallocHost(&sl.in_set, n) != cudaSuccess || cudaMallocHost(&sl.roots, 4 * n) != cudaSuccess ||
         cudaMallocHost(&sl.labels, 4 * n) != cudaSuccess || cudaMallocHost(&sl.c_rowptr, 4 * (n + 1)) != cudaSuccess ||
-        cudaMallocHost(&sl.c_colind, 4 * nnz) != cudaSuccess) {
+        cudaMallocHost(&sl.c_colind, 4 * nnz) != cudaSuccess || cudaMalloc(&sl.d_sum, 8) != cudaSuccess ||
+        cudaMallocHost(&sl.h_sum, 8) != cudaSuccess) {
       mis2_server_destroy(s);
       return MIS2_ERR_OUT_OF_MEMORY;
     }
@@ -201,9 +237,12 @@ int mis2_server_destroy(mis2_server* s) {
   for (auto& t : s->workers) t.join();
   for (auto& sl : s->slots) {
     if (sl.stream) cudaStreamDestroy(sl.stream);
+    if (sl.ctx && sl.ctx->coop_done) cudaEventDestroy(sl.ctx->coop_done);
     if (sl.ctx) mis2_ctx_destroy(sl.ctx);
-    for (void* p : {(void*)sl.in_set, (void*)sl.roots, (void*)sl.labels, (void*)sl.c_rowptr, (void*)sl.c_colind})
+    for (void* p : {(void*)sl.in_set, (void*)sl.roots, (void*)sl.labels, (void*)sl.c_rowptr, (void*)sl.c_colind,
+                    (void*)sl.h_sum})
       if (p) cudaFreeHost(p);
+    if (sl.d_sum) cudaFree(sl.d_sum);
   }
   delete s;
   return MIS2_OK;

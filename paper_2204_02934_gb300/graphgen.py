@@ -247,20 +247,33 @@ def mixed_batch(n_graphs: int = 512, lo: float = 1e3, hi: float = 2e5, seed: int
     return out
 
 
-def serving_pool(n_graphs: int = 64, seed: int = 11, max_side: int = 160, max_scale: int = 20):
-    """Request pool: 50/50 3D 7-pt grids (side log-uniform in [20, max_side])
-    and R-MAT graphs (scale uniform in [14, max_scale], average degree 16),
-    int32 rowptr."""
-    u = uniform01(np.arange(3 * n_graphs, dtype=np.uint64), seed)
-    out = []
-    for i in range(n_graphs):
-        if u[3 * i] < 0.5:
-            side = int(round(math.exp(math.log(20) + u[3 * i + 1] * (math.log(max_side) - math.log(20)))))
-            out.append(grid3d_7pt(side, side, side))
-        else:
-            sc = 14 + min(int(u[3 * i + 2] * (max_scale - 13)), max_scale - 14)
-            out.append(rmat(sc, 8, 0.57, 0.19, 0.19, seed * 7919 + i, np.int32))
-    return out
+def serving_graph(i: int, n_graphs: int = 64, seed: int = 11, max_side: int = 160, max_scale: int = 20) -> CSRGraph:
+    """Graph i of the request pool: a 3D 7-pt grid (side log-uniform in
+    [20, max_side]) or an R-MAT graph (scale uniform in [14, max_scale],
+    average degree 16), each with probability 1/2; int32 rowptr."""
+    u = uniform01(np.arange(3 * i, 3 * i + 3, dtype=np.uint64), seed)
+    if u[0] < 0.5:
+        side = int(round(math.exp(math.log(20) + u[1] * (math.log(max_side) - math.log(20)))))
+        return grid3d_7pt(side, side, side)
+    sc = 14 + min(int(u[2] * (max_scale - 13)), max_scale - 14)
+    return rmat(sc, 8, 0.57, 0.19, 0.19, seed * 7919 + i, np.int32)
+
+
+def _serving_graph_star(args):
+    return serving_graph(*args)
+
+
+def serving_pool(n_graphs: int = 64, seed: int = 11, max_side: int = 160, max_scale: int = 20,
+                 processes: int = 1) -> list:
+    """The request pool (serving_graph 0..n_graphs-1).  processes > 1 builds
+    the graphs in a spawned process pool (safe after CUDA is initialised)."""
+    jobs = [(i, n_graphs, seed, max_side, max_scale) for i in range(n_graphs)]
+    if processes <= 1:
+        return [serving_graph(*j) for j in jobs]
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(processes) as pool:
+        return pool.map(_serving_graph_star, jobs, chunksize=1)
 
 
 def poisson_arrivals(n_requests: int, rate_per_s: float, seed: int = 13) -> np.ndarray:

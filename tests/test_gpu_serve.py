@@ -22,19 +22,31 @@ def _built():
     _build.build()
 
 
-def _fnv(h, arr):
-    for byte in np.ascontiguousarray(arr, dtype="<i4").tobytes():
-        h ^= byte
-        h = (h * 1099511628211) & 0xFFFFFFFFFFFFFFFF
-    return h
+def _mix(z):
+    """SplitMix64 finaliser on a uint64 array (wrapping arithmetic)."""
+    z = z ^ (z >> np.uint64(30))
+    z = z * np.uint64(0xBF58476D1CE4E5B9)
+    z = z ^ (z >> np.uint64(27))
+    z = z * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def fingerprint(arrays, counts):
+    """The server's result fingerprint (mis2_result.checksum), restated."""
+    tot = np.zeros(1, dtype=np.uint64)
+    for k, a in enumerate(arrays):
+        i = np.arange(len(a), dtype=np.uint64)
+        x = np.ascontiguousarray(a, dtype=np.int32).view(np.uint32).astype(np.uint64)
+        tot += _mix(_mix((np.uint64(k) << np.uint64(40)) + i) ^ x).sum(dtype=np.uint64)
+    for j, c in enumerate(counts):
+        tot += _mix(np.array([((5 + j) << 40) ^ int(c)], dtype=np.uint64))
+    return int(tot[0])
 
 
 def _oracle_checksum(g, seed):
     lv = oracle.coarsen_level(g, seed=seed)
-    h = 1469598103934665603
-    for a in (lv.roots, lv.labels, lv.c_rowptr.astype(np.int32), lv.c_colind):
-        h = _fnv(h, a)
-    return h, lv
+    arrays = (lv.roots, lv.labels, lv.c_rowptr.astype(np.int32), lv.c_colind)
+    return fingerprint(arrays, (len(lv.roots), lv.n_aggs, len(lv.c_colind))), lv
 
 
 def _pool():
@@ -46,7 +58,8 @@ def _pool():
     return graphs, keep, host
 
 
-def test_results_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("loop", [mis2.MIS2_LOOP_DEVICE, mis2.MIS2_LOOP_HOST])
+def test_results_same_alone_and_in_the_mix(loop):
     graphs, keep, host = _pool()
     n_req = 80
     idx = (np.arange(n_req) * 7) % len(graphs)
@@ -54,7 +67,7 @@ def test_results_same_alone_and_in_the_mix():
     expect = [_oracle_checksum(g, 3)[0] for g in graphs]
     results = {}
     for slots in (1, 4):
-        srv = mis2.Server(slots=slots, slot_max_n=20000, slot_max_nnz=200000)
+        srv = mis2.Server(slots=slots, slot_max_n=20000, slot_max_nnz=200000, loop=loop)
         res, mif = srv.replay(host, arrivals, idx, seed=3)
         srv.close()
         assert all(r.status == 0 for r in res)
