@@ -28,8 +28,8 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim(GraphView<I> g, const int3
                                                       const int32_t* n_dev, int32_t* labels, int32_t base_host,
                                                       const int32_t* base_dev, int32_t* heavy, int32_t* heavy_cnt,
                                                       int32_t block_degree) {
-  const int64_t cnt = n_dev != nullptr ? *n_dev : n_host;
-  const int32_t base = base_dev != nullptr ? *base_dev : base_host;
+  const int64_t cnt = n_dev != nullptr ? block_load(n_dev) : n_host;
+  const int32_t base = base_dev != nullptr ? block_load(base_dev) : base_host;
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim_block(GraphView<I> g, cons
                                                             const int32_t* heavy, const int32_t* heavy_cnt,
                                                             int32_t* labels, int32_t base_host,
                                                             const int32_t* base_dev) {
-  const int64_t cnt = *heavy_cnt;
+  const int64_t cnt = block_load(heavy_cnt);
   const int32_t base = base_dev != nullptr ? *base_dev : base_host;
   for (int64_t h = blockIdx.x; h < cnt; h += gridDim.x) {
     const int32_t j = heavy[h];
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim_block(GraphView<I> g, cons
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_qualify(GraphView<I> g, const int32_t* list, const int32_t* n_dev,
                                                     const int32_t* labels, uint8_t* qflag) {
-  const int64_t cnt = *n_dev;
+  const int64_t cnt = block_load(n_dev);
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   const int lane = lane_id();
   int32_t* area = stage[threadIdx.x >> 5];
-  const int64_t cnt = *left_cnt;
+  const int64_t cnt = block_load(left_cnt);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < cnt; base += nw * 32) {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kBlock) k_phase3_sort(GraphView<I> g, const in
   __shared__ int32_t buf[kPhase3SortCap];
   __shared__ uint32_t sh[40];
   __shared__ int fill;
-  const int64_t n_items = *list_cnt;
+  const int64_t n_items = block_load(list_cnt);
   for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int32_t v = list[it];
     int64_t s, e;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kBlock) k_phase3_block(GraphView<I> g, const i
                                                          const int32_t* list_cnt, int32_t* labels, int32_t* err) {
   __shared__ int cnt[kPhase3Window];
   __shared__ uint32_t sh[40];
-  const int64_t n_items = *list_cnt;
+  const int64_t n_items = block_load(list_cnt);
   for (int64_t i = blockIdx.x; i < n_items; i += gridDim.x) {
     const int32_t v = list[i];
     int64_t s, e;

@@ -434,8 +434,8 @@ __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32
                                                      int32_t kb, const int64_t* chunk_off, uint32_t* bitmaps,
                                                      int64_t words, const int32_t* kb_dev) {
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
-  if (kb_dev != nullptr) kb = *kb_dev;
-  const int64_t total = chunk_off[kb];
+  if (kb_dev != nullptr) kb = block_load(kb_dev);
+  const int64_t total = block_load(chunk_off + kb);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t ch = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < total; ch += nw) {
     int lo = 0, hi = kb;  // last i with chunk_off[i] <= ch
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int
                                                        const int32_t* ub_ptr, uint32_t* bitmaps, int64_t words,
                                                        int32_t* tmp, int32_t* c_cnt, const int32_t* kb_dev) {
   __shared__ int sh[40];
-  if (kb_dev != nullptr) kb = *kb_dev;
+  if (kb_dev != nullptr) kb = block_load(kb_dev);
   for (int i = blockIdx.x; i < kb; i += gridDim.x) {
     const int32_t a = large[k0 + i];
     uint32_t* bm = bitmaps + (int64_t)i * words;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int
 
 // Clears the bitmaps of a batch whose size is only known on the device.
 __global__ void __launch_bounds__(kBlock) k_large_zero(uint32_t* bitmaps, int64_t words, const int32_t* kb_dev) {
-  const int64_t total = (int64_t)*kb_dev * words;
+  const int64_t total = (int64_t)block_load(kb_dev) * words;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     bitmaps[i] = 0u;
 }
@@ -494,9 +494,10 @@ __global__ void __launch_bounds__(kBlock) k_large_zero(uint32_t* bitmaps, int64_
 // batch or the coarse rows exceed the output capacity (and flags the latter).
 __device__ __forceinline__ bool pack_refused(const int32_t* err, const int32_t* total, int64_t cap) {
   if (err == nullptr) return false;
-  const bool over = *total > cap;
+  const bool over = block_load(total) > cap;
+  const int32_t e = block_load(err);
   if (over && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(const_cast<int32_t*>(err), kErrCapacity);
-  return over || (*err & kErrLargeOverflow) != 0;
+  return over || (e & kErrLargeOverflow) != 0;
 }
 
 constexpr int kPackWarpMax = 4096;  // longer coarse rows are copied by the whole grid
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* larg
                                                              int32_t* c_colind, const int32_t* err,
                                                              const int32_t* total, int64_t cap) {
   if (pack_refused(err, total, cap)) return;
-  const int64_t nl = *n_large;
+  const int64_t nl = block_load(n_large);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = 0; i < nl; i++) {
     const int32_t a = large[i];

@@ -217,6 +217,24 @@ __device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t* list,
 }
 
 // Add x over the warp into *acc with one 64-bit atomic (acc may be null).
+// *p read by one thread of the block and shared: one L2 request per block
+// where every warp of a large grid would otherwise read the same word.  Every
+// thread of the block must call it, in uniform control flow.
+__device__ __forceinline__ int32_t block_load(const int32_t* p) {
+  __shared__ int32_t v;
+  __syncthreads();
+  if (threadIdx.x == 0) v = *p;
+  __syncthreads();
+  return v;
+}
+__device__ __forceinline__ int64_t block_load(const int64_t* p) {
+  __shared__ int64_t v;
+  __syncthreads();
+  if (threadIdx.x == 0) v = *p;
+  __syncthreads();
+  return v;
+}
+
 __device__ __forceinline__ void warp_accumulate(int64_t x, int64_t* acc) {
   if (acc == nullptr) return;
 #pragma unroll

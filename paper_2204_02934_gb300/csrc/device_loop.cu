@@ -33,35 +33,33 @@ __device__ __forceinline__ int64_t global_ns() {
   return (int64_t)t;
 }
 
-// Sense-free generation barrier over all blocks of the grid.  Returns false
-// (in every thread of the block) when this block gave up waiting or another
-// block already reported a timeout.
-// ts (optional): the last block to arrive stores its arrival time in ts[0],
-// block 0 its departure time in ts[1] (globaltimer, ns).
-__device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t* gen, int32_t* err, int64_t spin_limit,
+// Grid barrier on a monotonic arrival counter (zeroed before the launch):
+// the k-th barrier of a launch (epoch k, counted by every block) completes
+// when the counter reaches k * gridDim.x.  Each block adds 1 after a fence
+// and polls with acquire loads; there is no reset step on the critical path.
+// Returns false (in every thread of the block) when this block gave up
+// waiting or another block already reported a timeout.
+// ts (optional): ts[0] = latest arrival time, ts[1] = block 0's departure
+// time (globaltimer, ns).
+__device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t& epoch, int32_t* err, int64_t spin_limit,
                                              int64_t* ts = nullptr) {
   __shared__ int ok;
   __syncthreads();
+  epoch++;
   if (threadIdx.x == 0) {
-    const int my_gen = ld_acquire_i32(gen);
-    __threadfence();
-    const int arrived = atomicAdd(count, 1);
     ok = 1;
-    if (arrived == (int)gridDim.x - 1) {
-      if (ts != nullptr) ts[0] = global_ns();
-      atomicExch(count, 0);
-      __threadfence();
-      st_release_i32(gen, my_gen + 1);
-    } else {
-      int64_t spins = 0;
-      while (ld_acquire_i32(gen) == my_gen) {
-        if (++spins > spin_limit || (ld_volatile_i32(err) & kErrTimeout)) {
-          atomicOr(err, kErrTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+    if (ts != nullptr) atomicMax(reinterpret_cast<unsigned long long*>(ts), (unsigned long long)global_ns());
+    __threadfence();
+    atomicAdd(count, 1);
+    const uint32_t target = (uint32_t)epoch * gridDim.x;
+    int64_t spins = 0;
+    while ((int32_t)((uint32_t)ld_acquire_i32(count) - target) < 0) {
+      if (++spins > spin_limit || (ld_volatile_i32(err) & kErrTimeout)) {
+        atomicOr(err, kErrTimeout);
+        ok = 0;
+        break;
       }
+      __nanosleep(32);
     }
     __threadfence();
     if (ts != nullptr && blockIdx.x == 0) ts[1] = global_ns();
@@ -89,11 +87,12 @@ struct LoopArgs {
 template <int G, typename I>
 __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
   __shared__ uint32_t sh[40];
+  __shared__ int32_t sh_n[2 * kClasses];
   __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
   int32_t* my_stage = stage[threadIdx.x >> 5];
   int32_t* ctr = a.ctr;
   int32_t* bar_count = ctr + kCtrBarrier;
-  int32_t* bar_gen = ctr + kCtrBarrier + 1;
+  int32_t epoch = 0;
   int32_t* err = ctr + kCtrErr;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -103,17 +102,23 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
                    a.warp_degree, a.block_degree, tid, nthreads);
   int64_t* ts = a.ts;
   if (ts != nullptr && tid == 0) ts[0] = global_ns();  // start of the launch
-  if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts ? ts + 2 : nullptr)) return;
+  if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr)) return;
 
   int r = 0;
   for (;; r++) {
     const int slot = r % 3, nslot = (r + 1) % 3, zslot = (r + 2) % 3;
+    // the worklist sizes: read once per block (one request instead of one
+    // per warp on the same L2 line) and shared
+    if (threadIdx.x < 2 * kClasses)
+      sh_n[threadIdx.x] = ld_volatile_i32(ctr + (threadIdx.x < kClasses ? ctr_c1(slot, (int)threadIdx.x)
+                                                                         : ctr_c2(slot, (int)threadIdx.x - kClasses)));
+    __syncthreads();
     int n1[kClasses], n2[kClasses];
     int w1 = 0, w2 = 0;
 #pragma unroll
     for (int k = 0; k < kClasses; k++) {
-      n1[k] = ld_volatile_i32(ctr + ctr_c1(slot, k));
-      n2[k] = ld_volatile_i32(ctr + ctr_c2(slot, k));
+      n1[k] = sh_n[k];
+      n2[k] = sh_n[kClasses + k];
       w1 += n1[k];
       w2 += n2[k];
     }
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
       column_block_rows<I, false>(g, a.T, a.M, in2.l[2], n2[2], out2.l[2], ctr + ctr_c2(nslot, 2), d2, blockIdx.x,
                                   gridDim.x, sh);
     const bool ts_on = ts != nullptr && r < MIS2_TRACE_CAP;
-    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr)) return;
+    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr)) return;
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = w1;
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     if (n1[2] > 0)
       decide_block_rows<I, false>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
                                   (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
-    if (!grid_barrier(bar_count, bar_gen, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr)) return;
+    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr)) return;
   }
   if (tid == 0) ctr[a.rounds_slot] = r;
 }
@@ -223,6 +228,7 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
     MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrBarrier, 0, 2 * sizeof(int32_t), st));
   }
   MIS2_CUDA(cudaMemsetAsync(la.dtr, 0, MIS2_TRACE_CAP * 4 * sizeof(int64_t), st));
+  if (la.ts != nullptr) MIS2_CUDA(cudaMemsetAsync(la.ts, 0, kLoopTsWords * sizeof(int64_t), st));
   timer_begin(c, kKcDeviceLoop, st);
   int rc;
   switch (pick_group_lanes(c, g)) {

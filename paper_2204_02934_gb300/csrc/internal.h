@@ -29,7 +29,7 @@ enum : int {
   kCtrCnnz = 25,     // coarse nnz
   kCtrErr = 26,      // device error flags (bit 0: barrier timeout)
   kCtrRounds = 27,   // rounds of the device loop
-  kCtrBarrier = 28,  // grid barrier: arrive count (28), generation (29)
+  kCtrBarrier = 28,  // grid barrier: monotonic arrival count (28; 29 unused)
   kCtrLeftMid = 30,  // phase-3 leftovers of medium degree
   kCtrRounds2 = 32,  // rounds of the phase-2 device loop
   kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch

@@ -40,7 +40,8 @@ __global__ void __launch_bounds__(kBlock) k_column(GraphView<I> g, const uint32_
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  column_group_rows<G, I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, tr.d, warp, nw);
+  column_group_rows<G, I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, warp,
+                                nw);
 }
 
 template <int G, typename I>
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(kBlock) k_decide(GraphView<I> g, uint32_t* T, 
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  decide_group_rows<G, I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, tr.d, p, next_iter, warp, nw);
+  decide_group_rows<G, I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, p, next_iter, warp,
+                                nw);
 }
 
 template <typename I>
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(kBlock) k_column_lane(GraphView<I> g, const ui
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  column_lane_rows<I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, tr.d, warp, nw, stage[threadIdx.x >> 5]);
+  column_lane_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, warp, nw,
+                            stage[threadIdx.x >> 5]);
 }
 
 template <typename I>
@@ -74,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_decide_lane(GraphView<I> g, uint32_t
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  decide_lane_rows<I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, tr.d, p, next_iter, warp, nw,
+  decide_lane_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, p, next_iter, warp, nw,
                             stage[threadIdx.x >> 5]);
 }
 
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(kBlock) k_column_block(GraphView<I> g, const u
                                                          const int32_t* wl_in, const int32_t* cnt_in,
                                                          int32_t* wl_out, int32_t* cnt_out, int64_t* dsum) {
   __shared__ uint32_t sh[40];
-  column_block_rows<I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, dsum, blockIdx.x, gridDim.x, sh);
+  column_block_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, dsum, blockIdx.x, gridDim.x, sh);
 }
 
 template <typename I>
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_decide_block(GraphView<I> g, uint32_
                                                          int32_t* wl_out, int32_t* cnt_out, int64_t* dsum,
                                                          PrioCfg p, uint32_t next_iter) {
   __shared__ uint32_t sh[40];
-  decide_block_rows<I, true>(g, T, M, wl_in, *cnt_in, wl_out, cnt_out, dsum, p, next_iter, blockIdx.x,
+  decide_block_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, dsum, p, next_iter, blockIdx.x,
                              gridDim.x, sh);
 }
 

@@ -69,9 +69,10 @@ struct WarpAppender {
 
 // Stage each lane's row colind[s, s + len) (len <= kLaneRowMax, or len < 0:
 // not staged) in the warp's shared area and return where this lane's row
-// starts there.  When the 32 rows are back to back in colind (worklists that
-// still hold runs of consecutive vertices), the whole span moves with 16-byte
-// copies, 512 contiguous bytes per instruction; otherwise each row moves with
+// starts there.  When the 32 rows lie in ascending order in colind with
+// little in between (worklists that still hold runs of consecutive vertices,
+// possibly with holes), the whole span moves with 16-byte copies, 512
+// contiguous bytes per instruction, gaps included; otherwise each row moves with
 // one coalesced 4-byte copy per entry, into padded per-lane slots (4 rows
 // per copy instruction when no row is longer than 8, 2 when none is longer
 // than 16).  Every lane of the warp must call this; on return every staged
@@ -86,12 +87,15 @@ __device__ __forceinline__ const int32_t* stage_rows_warp(const int32_t* __restr
   if (width != nullptr) *width = wd;
   const int64_t s_next = __shfl_down_sync(kFull, s, 1);
   const int64_t e = s + (len > 0 ? len : 0);
-  const bool joined = lane == 31 || e == s_next;
+  const bool ordered = lane == 31 || e <= s_next;
   const int64_t s0 = __shfl_sync(kFull, s, 0);
   const int64_t e31 = __shfl_sync(kFull, e, 31);
   const int64_t a = s0 & ~int64_t(3);
   const int64_t nq = (e31 - a + 3) >> 2;
-  if (vec && __all_sync(kFull, len >= 0 && joined) && nq * 4 <= kStageWarpWords && a + nq * 4 <= nnz) {
+  // copied words at most 1.5x the staged ones (plus alignment slack)
+  const int64_t useful = __reduce_add_sync(kFull, (unsigned)(len > 0 ? len : 0));
+  if (vec && __all_sync(kFull, len >= 0 && ordered) && nq * 4 <= kStageWarpWords && a + nq * 4 <= nnz &&
+      2 * nq * 4 <= 3 * useful + 64) {
     for (int64_t q = lane; q < nq; q += 32) cp_async16(area + 4 * q, colind + a + 4 * q);
     cp_async_wait_all();
     __syncwarp();
