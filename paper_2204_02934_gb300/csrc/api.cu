@@ -167,6 +167,10 @@ static int alloc_scratch(mis2_ctx* c) {
   MIS2_TRY(dev_alloc(c, &s.labels_tmp, n));
   MIS2_TRY(dev_alloc(c, &s.bitmaps, (int64_t)coarse_bitmap_blocks(c) * ((n + 31) / 32)));
   MIS2_TRY(dev_alloc(c, &s.chunk_off, n + 1));
+  const int64_t giant_cap = nnz / kGiantRow + 1;
+  MIS2_TRY(dev_alloc(c, &s.giant_v, giant_cap));
+  MIS2_TRY(dev_alloc(c, &s.giant_slot, giant_cap));
+  MIS2_TRY(dev_alloc(c, &s.giant_off, giant_cap + 1));
   if (cudaMallocHost(&c->h_ctr, kCtrWords * sizeof(int32_t)) != cudaSuccess) return MIS2_ERR_OUT_OF_MEMORY;
   if (cudaMallocHost(&c->h_trace, 2 * MIS2_TRACE_CAP * 4 * sizeof(int64_t)) != cudaSuccess)
     return MIS2_ERR_OUT_OF_MEMORY;
@@ -413,7 +417,7 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
     MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MIS2_CUDA(cudaStreamSynchronize(st));
     if (coarsen_fast_needs_retry(c)) {
-      MIS2_TRY(coarsen_impl(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, &cn, st));
+      MIS2_TRY(coarsen_fast_finish(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, &cn, st));
     } else {
       if (c->h_ctr[kCtrErr] & kErrCapacity) return MIS2_ERR_INVALID_ARG;
       cn = c->h_ctr[kCtrCnnz];

@@ -92,9 +92,20 @@ __device__ __forceinline__ void staged_labels(const int32_t* labels, const int32
 // is absent or belongs to a itself; every lane calls it with its own array
 // (32 entries for a staged member row, 4 per step of a long row), so a
 // callback can issue all its memory operations before waiting on any.
+// Member rows longer than kGiantRow found while walking a large aggregate
+// are handed to this list instead (vertex, bitmap slot) and walked later in
+// pieces by the whole grid.
+struct GiantList {
+  int32_t* v;
+  int32_t* slot;
+  int32_t* cnt;
+  int32_t cur_slot;
+};
+
 template <typename I, typename FB>
 __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int32_t* labels, const int32_t* members,
-                                               int64_t mb, int64_t me, int32_t a, int32_t* stage_warp, FB&& fb) {
+                                               int64_t mb, int64_t me, int32_t a, int32_t* stage_warp, FB&& fb,
+                                               const GiantList* giant = nullptr) {
   const int lane = lane_id();
   for (int64_t kb = mb; kb < me; kb += 32) {
     const int64_t k = kb + lane;
@@ -110,7 +121,21 @@ __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int3
       else staged_labels<32>(labels, mine, len, a, fb);
     }
     __syncwarp();
-    unsigned longm = __ballot_sync(kFull, has && len < 0);
+    if (giant != nullptr) {
+      const bool gi = has && e - s > kGiantRow;
+      const unsigned gm = __ballot_sync(kFull, gi);
+      if (gm) {
+        int base = 0;
+        if (lane == __ffs(gm) - 1) base = atomicAdd(giant->cnt, __popc(gm));
+        base = __shfl_sync(kFull, base, __ffs(gm) - 1);
+        if (gi) {
+          const int idx = base + __popc(gm & ((1u << lane) - 1u));
+          giant->v[idx] = members[k];
+          giant->slot[idx] = giant->cur_slot;
+        }
+      }
+    }
+    unsigned longm = __ballot_sync(kFull, has && len < 0 && (giant == nullptr || e - s <= kGiantRow));
     while (longm) {
       const int j = __ffs(longm) - 1;
       longm &= longm - 1;
@@ -217,7 +242,9 @@ __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const i
     const int32_t p0 = in ? agg_ptr[a] : 0;
     const int32_t p1 = in ? agg_ptr[a + 1] : 0;
     const int32_t u = in ? ub[a] : 0;
-    const bool sm = in && small_aggregate(p1 - p0, u, true);
+    // an aggregate without fine entries (an isolated vertex) has an empty row
+    if (in && u == 0) c_cnt[a] = 0;
+    const bool sm = in && u > 0 && small_aggregate(p1 - p0, u, true);
     const int32_t outb = sm ? ub_ptr[a] : 0;
     const int m = sm ? p1 - p0 : 0;
     const int um = sm ? u : 0;
@@ -352,6 +379,10 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
       for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++) {
         const int32_t l = lab[j];
         if (l < 0 || l == prev) continue;
+        // past the distinct cap the aggregate goes to the bitmap path: stop
+        // inserting (each lane has at most one insert in flight past the cap,
+        // so the table never fills and probing ends)
+        if (*reinterpret_cast<volatile int32_t*>(scnt + wib) > kDistinctCap) break;
         prev = l;
         uint32_t h = label_hash(l);
         for (int probe = 0; probe < kHashSlots; probe++) {
@@ -410,29 +441,115 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
 // With n_large_dev set (single-batch path), the batch is the first
 // min(kb, n_large) large aggregates, that count goes to *kb_out, and a larger
 // n_large raises kErrLargeOverflow.
-__global__ void k_large_chunks(const int32_t* large, int32_t k0, int32_t kb, const int32_t* agg_ptr,
-                               int64_t* chunk_off, const int32_t* n_large_dev, int32_t* kb_out, int32_t* err) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  if (n_large_dev != nullptr) {
-    const int32_t nl = *n_large_dev;
-    if (nl > kb) atomicOr(err, kErrLargeOverflow);
-    kb = min(kb, nl);
-    *kb_out = kb;
+// One block (kBlock threads) scans the batch in tiles.  It also clears the
+// batch's giant-row list.
+__global__ void __launch_bounds__(kBlock) k_large_chunks(const int32_t* large, int32_t k0, int32_t kb,
+                                                         const int32_t* agg_ptr, int64_t* chunk_off,
+                                                         const int32_t* n_large_dev, int32_t* kb_out, int32_t* err,
+                                                         int32_t* giant_cnt) {
+  __shared__ int sh[40];
+  __shared__ int32_t skb;
+  if (threadIdx.x == 0) {
+    int32_t b = kb;
+    if (n_large_dev != nullptr) {
+      const int32_t nl = *n_large_dev;
+      if (nl > kb) atomicOr(err, kErrLargeOverflow);
+      b = min(kb, nl);
+      *kb_out = b;
+    }
+    skb = b;
+    *giant_cnt = 0;
   }
+  __syncthreads();
+  kb = skb;
   int64_t acc = 0;
-  for (int i = 0; i < kb; i++) {
-    chunk_off[i] = acc;
-    const int32_t a = large[k0 + i];
-    acc += (agg_ptr[a + 1] - agg_ptr[a] + 31) / 32;
+  for (int t0 = 0; t0 < kb; t0 += kBlock) {
+    const int i = t0 + threadIdx.x;
+    int c = 0;
+    if (i < kb) {
+      const int32_t a = large[k0 + i];
+      c = (agg_ptr[a + 1] - agg_ptr[a] + 31) / 32;
+    }
+    int tile_total;
+    const int x = block_exclusive_scan(c, sh, &tile_total);
+    if (i < kb) chunk_off[i] = acc + x;
+    acc += tile_total;
   }
-  chunk_off[kb] = acc;
+  if (threadIdx.x == 0) chunk_off[kb] = acc;
+}
+
+// Piece offsets of the giant rows (kGiantRow entries per piece), one block.
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_giant_pieces(GraphView<I> g, const int32_t* giant_v,
+                                                         const int32_t* giant_cnt, int64_t* giant_off) {
+  __shared__ int sh[40];
+  const int32_t ng = block_load(giant_cnt);
+  int64_t acc = 0;
+  for (int t0 = 0; t0 < ng; t0 += kBlock) {
+    const int i = t0 + threadIdx.x;
+    int c = 0;
+    if (i < ng) {
+      int64_t s, e;
+      row_range(g, giant_v[i], s, e);
+      c = (int)((e - s + kGiantRow - 1) / kGiantRow);
+    }
+    int tile_total;
+    const int x = block_exclusive_scan(c, sh, &tile_total);
+    if (i < ng) giant_off[i] = acc + x;
+    acc += tile_total;
+  }
+  if (threadIdx.x == 0) giant_off[ng] = acc;
+}
+
+// Every warp of the grid takes pieces of giant rows and ORs their labels into
+// the row's bitmap.
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_giant_or(GraphView<I> g, const int32_t* labels, const int32_t* large,
+                                                     int32_t k0, const int32_t* giant_v, const int32_t* giant_slot,
+                                                     const int32_t* giant_cnt, const int64_t* giant_off,
+                                                     uint32_t* bitmaps, int64_t words) {
+  const int32_t ng = block_load(giant_cnt);
+  const int64_t total = block_load(giant_off + ng);
+  const int lane = lane_id();
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t pc = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; pc < total; pc += nw) {
+    int lo = 0, hi = ng;  // last i with giant_off[i] <= pc
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (giant_off[mid] <= pc) lo = mid;
+      else hi = mid;
+    }
+    const int32_t slot = giant_slot[lo];
+    const int32_t a = large[k0 + slot];
+    int64_t s, e;
+    row_range(g, giant_v[lo], s, e);
+    const int64_t ps = s + (pc - giant_off[lo]) * kGiantRow;
+    const int64_t pe = min(e, ps + kGiantRow);
+    uint32_t* bm = bitmaps + (int64_t)slot * words;
+    for (int64_t p = (ps & ~int64_t(3)) + 4 * lane; p < pe; p += 128) {
+      int32_t w4[4];
+      if (g.vec && p + 4 <= g.nnz) {
+        const int4 q = __ldg(reinterpret_cast<const int4*>(g.colind + p));
+        w4[0] = q.x, w4[1] = q.y, w4[2] = q.z, w4[3] = q.w;
+      } else {
+#pragma unroll
+        for (int t = 0; t < 4; t++) w4[t] = (p + t >= ps && p + t < pe) ? g.colind[p + t] : 0;
+      }
+#pragma unroll
+      for (int t = 0; t < 4; t++) {
+        const int32_t l = (p + t >= ps && p + t < pe) ? labels[w4[t]] : a;
+        if (l != a) atomicOr(bm + (l >> 5), 1u << (l & 31));
+      }
+    }
+  }
 }
 
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32_t* labels, const int32_t* agg_ptr,
                                                      const int32_t* members, const int32_t* large, int32_t k0,
                                                      int32_t kb, const int64_t* chunk_off, uint32_t* bitmaps,
-                                                     int64_t words, const int32_t* kb_dev) {
+                                                     int64_t words, const int32_t* kb_dev, int32_t* giant_v,
+                                                     int32_t* giant_slot, int32_t* giant_cnt) {
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   if (kb_dev != nullptr) kb = block_load(kb_dev);
   const int64_t total = block_load(chunk_off + kb);
@@ -448,38 +565,69 @@ __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32
     const int64_t mb = agg_ptr[a] + (ch - chunk_off[lo]) * 32;
     const int64_t me = min((int64_t)agg_ptr[a + 1], mb + 32);
     uint32_t* bm = bitmaps + (int64_t)lo * words;
-    walk_aggregate<I>(g, labels, members, mb, me, a, stage[threadIdx.x >> 5], [&](auto& lab) {
+    const GiantList gl{giant_v, giant_slot, giant_cnt, lo};
+    walk_aggregate<I>(
+        g, labels, members, mb, me, a, stage[threadIdx.x >> 5],
+        [&](auto& lab) {
 #pragma unroll
-      for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++)
-        if (lab[j] >= 0) atomicOr(bm + (lab[j] >> 5), 1u << (lab[j] & 31));
-    });
+          for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++)
+            if (lab[j] >= 0) atomicOr(bm + (lab[j] >> 5), 1u << (lab[j] & 31));
+        },
+        &gl);
   }
 }
 
+// One block per bitmap: each warp owns a contiguous run of words; a first
+// pass counts the set bits per warp (one block-level exchange per bitmap),
+// a second writes the labels of the warp's non-zero words in ascending order
+// behind the counts of the warps before it, and clears those words.
 __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int32_t k0, int32_t kb,
                                                        const int32_t* ub_ptr, uint32_t* bitmaps, int64_t words,
                                                        int32_t* tmp, int32_t* c_cnt, const int32_t* kb_dev) {
-  __shared__ int sh[40];
+  constexpr int kW = kBlock / 32;
+  __shared__ int64_t wsum[kW];
   if (kb_dev != nullptr) kb = block_load(kb_dev);
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const int64_t seg = ((words + kW - 1) / kW + 31) / 32 * 32;
+  const int64_t w0 = min(words, (int64_t)w * seg), w1 = min(words, w0 + seg);
   for (int i = blockIdx.x; i < kb; i += gridDim.x) {
     const int32_t a = large[k0 + i];
     uint32_t* bm = bitmaps + (int64_t)i * words;
     const int64_t out = ub_ptr[a];
-    int64_t run = 0;
-    for (int64_t wb = 0; wb < words; wb += blockDim.x) {
-      const int64_t wi = wb + threadIdx.x;
-      uint32_t w = wi < words ? bm[wi] : 0u;
-      int total;
-      int pos = block_exclusive_scan(__popc(w), sh, &total);
-      if (w != 0u) bm[wi] = 0u;
-      while (w) {
-        const int bit = __ffs(w) - 1;
-        w &= w - 1;
-        tmp[out + run + pos++] = (int32_t)(wi * 32 + bit);
-      }
-      run += total;
+    int64_t cnt = 0;
+    for (int64_t j = w0 + lane; j < w1; j += 32) cnt += __popc(bm[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if (lane == 0) wsum[w] = cnt;
+    __syncthreads();
+    int64_t run = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < kW; k++) {
+      run += k < w ? wsum[k] : 0;
+      total += wsum[k];
     }
-    if (threadIdx.x == 0) c_cnt[a] = (int32_t)run;
+    for (int64_t j0 = w0; j0 < w1; j0 += 32) {
+      const int64_t j = j0 + lane;
+      uint32_t x = j < w1 ? bm[j] : 0u;
+      if (__ballot_sync(kFull, x != 0u) == 0u) continue;
+      const int c = __popc(x);
+      int incl = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int pos = incl - c;
+      if (x != 0u) bm[j] = 0u;
+      while (x) {
+        const int bit = __ffs(x) - 1;
+        x &= x - 1;
+        tmp[out + run + pos++] = (int32_t)(j * 32 + bit);
+      }
+      run += __shfl_sync(kFull, incl, 31);
+    }
+    if (threadIdx.x == 0) c_cnt[a] = (int32_t)total;
+    __syncthreads();
   }
 }
 
@@ -517,8 +665,8 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const in
   }
 }
 
-// Rows longer than kPackWarpMax (only large aggregates have them): every
-// block copies a slice of each.
+// Rows longer than kPackWarpMax (only large aggregates have them): a block
+// per row.
 __global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* large, const int32_t* n_large,
                                                              const int32_t* ub_ptr, const int32_t* c_cnt,
                                                              const int32_t* c_rowptr, const int32_t* tmp,
@@ -526,14 +674,12 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* larg
                                                              const int32_t* total, int64_t cap) {
   if (pack_refused(err, total, cap)) return;
   const int64_t nl = block_load(n_large);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = 0; i < nl; i++) {
+  for (int64_t i = blockIdx.x; i < nl; i += gridDim.x) {
     const int32_t a = large[i];
     const int64_t len = c_cnt[a];
     if (len <= kPackWarpMax) continue;
     const int64_t src = ub_ptr[a], dst = c_rowptr[a];
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += stride)
-      c_colind[dst + k] = tmp[src + k];
+    for (int64_t k = threadIdx.x; k < len; k += blockDim.x) c_colind[dst + k] = tmp[src + k];
   }
 }
 
@@ -542,6 +688,76 @@ int coarse_bitmap_blocks(const mis2_ctx* c) {
   const int64_t words = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
   const int64_t cap = ((int64_t)256 << 20) / (words * 4);
   return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->sm_count * 2, cap));
+}
+
+template <typename I>
+static GraphView<I> gview_of(const GraphArgs& g) {
+  GraphView<I> gv;
+  gv.rowptr = static_cast<const I*>(g.rowptr);
+  gv.colind = g.colind;
+  gv.n = g.n;
+  gv.nnz = g.nnz;
+  gv.vec = g.vec ? 1 : 0;
+  gv.pad = 0;
+  return gv;
+}
+
+// Bitmaps per batch of large aggregates: as many as fit the bitmap scratch
+// (sized for the context's largest graph), at most n_aggs.
+static int32_t bitmap_slots(const mis2_ctx* c, int64_t n_aggs) {
+  const int64_t words = (std::max<int64_t>(n_aggs, 1) + 31) / 32;
+  const int64_t words_cap = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)coarse_bitmap_blocks(c) * words_cap / words,
+                                                          std::max<int64_t>(n_aggs, 1)));
+}
+
+// Large aggregates k_start..n_large-1 in batches of bitmaps, then the row
+// offsets (one host read of the total) and the packed colind.
+template <typename I>
+static int coarse_tail(mis2_ctx* c, const GraphView<I>& gv, const int32_t* labels, int64_t n_aggs, int32_t n_large,
+                       int32_t k_start, int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz,
+                       cudaStream_t st) {
+  Scratch& s = c->s;
+  if (n_large > k_start) {
+    const int64_t words = (n_aggs + 31) / 32;
+    const int32_t slots = bitmap_slots(c, n_aggs);
+    timer_begin(c, kKcCoarse, st);
+    for (int32_t k0 = k_start; k0 < n_large; k0 += slots) {
+      const int32_t kb = std::min(slots, n_large - k0);
+      MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)kb * words * sizeof(uint32_t), st));
+      k_large_chunks<<<1, kBlock, 0, st>>>(s.large, k0, kb, s.agg_ptr, s.chunk_off, nullptr, nullptr, nullptr,
+                                           s.ctr + kCtrGiant);
+      k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, k0, kb,
+                                                        s.chunk_off, s.bitmaps, words, nullptr, s.giant_v,
+                                                        s.giant_slot, s.ctr + kCtrGiant);
+      k_giant_pieces<I><<<1, kBlock, 0, st>>>(gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
+      k_giant_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.large, k0, s.giant_v, s.giant_slot,
+                                                        s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
+      k_large_emit<<<std::min<int32_t>(kb, c->sm_count * 2), kBlock, 0, st>>>(s.large, k0, kb, s.ub_ptr, s.bitmaps,
+                                                                             words, s.tmp, s.c_cnt, nullptr);
+      c->launches += 5;
+    }
+    timer_end(c, st);
+    MIS2_CUDA(cudaGetLastError());
+  }
+  MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
+  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MIS2_CUDA(cudaStreamSynchronize(st));
+  const int64_t total = c->h_ctr[kCtrCnnz];
+  if (total > c_colind_cap) return MIS2_ERR_INVALID_ARG;
+  timer_begin(c, kKcCoarse, st);
+  k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
+                                                                        c_colind, nullptr, nullptr, 0);
+  c->launches++;
+  if (n_large > 0) {
+    k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
+                                                           s.tmp, c_colind, nullptr, nullptr, 0);
+    c->launches++;
+  }
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  *c_nnz = total;
+  return MIS2_OK;
 }
 
 template <typename I>
@@ -590,50 +806,15 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   // large aggregates, in batches of `slots` bitmaps
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MIS2_CUDA(cudaStreamSynchronize(st));
-  const int32_t n_large = c->h_ctr[kCtrLarge];
-  if (n_large > 0) {
-    const int64_t words = (n_aggs + 31) / 32;
-    const int64_t words_cap = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
-    const int32_t slots = (int32_t)std::max<int64_t>(1, (int64_t)coarse_bitmap_blocks(c) * words_cap / words);
-    timer_begin(c, kKcCoarse, st);
-    for (int32_t k0 = 0; k0 < n_large; k0 += slots) {
-      const int32_t kb = std::min(slots, n_large - k0);
-      MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)kb * words * sizeof(uint32_t), st));
-      k_large_chunks<<<1, 32, 0, st>>>(s.large, k0, kb, s.agg_ptr, s.chunk_off, nullptr, nullptr, nullptr);
-      k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, k0, kb,
-                                                        s.chunk_off, s.bitmaps, words, nullptr);
-      k_large_emit<<<std::min<int32_t>(kb, c->sm_count * 2), kBlock, 0, st>>>(s.large, k0, kb, s.ub_ptr, s.bitmaps,
-                                                                             words, s.tmp, s.c_cnt, nullptr);
-      c->launches += 3;
-    }
-    timer_end(c, st);
-    MIS2_CUDA(cudaGetLastError());
-  }
-  MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
-  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  MIS2_CUDA(cudaStreamSynchronize(st));
-  const int64_t total = c->h_ctr[kCtrCnnz];
-  if (total > c_colind_cap) return MIS2_ERR_INVALID_ARG;
-  timer_begin(c, kKcCoarse, st);
-  k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
-                                                                        c_colind, nullptr, nullptr, 0);
-  c->launches++;
-  if (n_large > 0) {
-    k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
-                                                           s.tmp, c_colind, nullptr, nullptr, 0);
-    c->launches++;
-  }
-  timer_end(c, st);
-  MIS2_CUDA(cudaGetLastError());
-  *c_nnz = total;
-  return MIS2_OK;
+  return coarse_tail<I>(c, gv, labels, n_aggs, c->h_ctr[kCtrLarge], 0, c_rowptr, c_colind, c_colind_cap, c_nnz, st);
 }
 
 // The same coarse graph without a host round trip: the large aggregates go
 // through one bitmap batch sized on the host from n_aggs, whose count is read
 // on the device; the output capacity is checked on the device.  More large
-// aggregates than one batch holds set kErrLargeOverflow and the caller reruns
-// the batched path (coarsen_fast_needs_retry).
+// aggregates than one batch holds set kErrLargeOverflow; the caller then
+// finishes the remaining batches (coarsen_fast_needs_retry,
+// coarsen_fast_finish).
 template <typename I>
 static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                           int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st) {
@@ -676,17 +857,19 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
                                                          s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on);
   const int64_t words = (n_aggs + 31) / 32;
-  const int64_t words_cap = (std::max<int64_t>(c->max_n, 1) + 31) / 32;
-  const int32_t slots = (int32_t)std::max<int64_t>(
-      1, std::min<int64_t>((int64_t)coarse_bitmap_blocks(c) * words_cap / words, std::max<int64_t>(n_aggs, 1)));
-  k_large_chunks<<<1, 32, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
-                                   s.ctr + kCtrLargeKb, s.ctr + kCtrErr);
+  const int32_t slots = bitmap_slots(c, n_aggs);
+  k_large_chunks<<<1, kBlock, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
+                                       s.ctr + kCtrLargeKb, s.ctr + kCtrErr, s.ctr + kCtrGiant);
   k_large_zero<<<c->sm_count * 2, kBlock, 0, st>>>(s.bitmaps, words, s.ctr + kCtrLargeKb);
   k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, 0, slots,
-                                                    s.chunk_off, s.bitmaps, words, s.ctr + kCtrLargeKb);
+                                                    s.chunk_off, s.bitmaps, words, s.ctr + kCtrLargeKb, s.giant_v,
+                                                    s.giant_slot, s.ctr + kCtrGiant);
+  k_giant_pieces<I><<<1, kBlock, 0, st>>>(gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
+  k_giant_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.large, 0, s.giant_v, s.giant_slot,
+                                                    s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
   k_large_emit<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, 0, slots, s.ub_ptr, s.bitmaps, words, s.tmp, s.c_cnt,
                                                    s.ctr + kCtrLargeKb);
-  c->launches += 6;
+  c->launches += 8;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
@@ -710,6 +893,20 @@ int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t
 }
 
 bool coarsen_fast_needs_retry(const mis2_ctx* c) { return (c->h_ctr[kCtrErr] & kErrLargeOverflow) != 0; }
+
+// After a single-batch pass that overflowed (counters read back into
+// c->h_ctr): the remaining large aggregates, the row offsets and the packing.
+int coarsen_fast_finish(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
+                        int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st) {
+  const int32_t n_large = c->h_ctr[kCtrLarge];
+  const int32_t done = bitmap_slots(c, n_aggs);
+  MIS2_CUDA(cudaMemsetAsync(c->s.ctr + kCtrErr, 0, sizeof(int32_t), st));
+  if (g.rp64)
+    return coarse_tail<int64_t>(c, gview_of<int64_t>(g), labels, n_aggs, n_large, done, c_rowptr, c_colind,
+                                c_colind_cap, c_nnz, st);
+  return coarse_tail<int32_t>(c, gview_of<int32_t>(g), labels, n_aggs, n_large, done, c_rowptr, c_colind,
+                              c_colind_cap, c_nnz, st);
+}
 
 int coarsen_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                  int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st) {

@@ -33,12 +33,16 @@ enum : int {
   kCtrLeftMid = 30,  // phase-3 leftovers of medium degree
   kCtrRounds2 = 32,  // rounds of the phase-2 device loop
   kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch
+  kCtrGiant = 34,    // giant member rows of the current bitmap batch
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 40;
+// Member rows of large aggregates longer than this are split into pieces of
+// this many entries, spread over the grid (coarse graph).
+constexpr int kGiantRow = 4096;
 // device error flags (ctr[kCtrErr])
 // kErrLargeOverflow: more large aggregates than one bitmap batch holds, seen
-// by the single-batch coarse path (the caller reruns the batched path).
+// by the single-batch coarse path (the caller finishes the other batches).
 enum : int {
   kErrTimeout = 1,
   kErrNoAggregatedNeighbour = 2,
@@ -88,6 +92,9 @@ struct Scratch {
   int32_t* tmp = nullptr;        // coarse rows before packing (max_nnz)
   uint32_t* bitmaps = nullptr;   // coarse graph: bitmaps over aggregate ids for large aggregates
   int64_t* chunk_off = nullptr;  // coarse graph: member-chunk offsets of a batch of large aggregates
+  int32_t* giant_v = nullptr;     // coarse graph: member rows longer than kGiantRow of a bitmap batch,
+  int32_t* giant_slot = nullptr;  //   their bitmap slot,
+  int64_t* giant_off = nullptr;   //   and their piece offsets (capacity nnz / kGiantRow + 1)
   int32_t* labels_tmp = nullptr; // labels when the caller passes none
 };
 
@@ -199,12 +206,15 @@ int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, 
 // ctr[kCtrErr].
 int agg_level_async(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const PrioCfg& p, int mode, int32_t* labels,
                     cudaStream_t st);
-// Coarse graph without host synchronisation; the caller synchronises and
-// then checks coarsen_fast_needs_retry (more large aggregates than one batch
-// of bitmaps, or a c_colind too small) before trusting the result.
+// Coarse graph without host synchronisation; the caller synchronises, reads
+// the counters into c->h_ctr and checks coarsen_fast_needs_retry (more large
+// aggregates than one batch of bitmaps: coarsen_fast_finish completes the
+// result) and kErrCapacity (c_colind too small) before trusting the result.
 int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                  int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st);
 bool coarsen_fast_needs_retry(const mis2_ctx* c);
+int coarsen_fast_finish(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
+                        int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st);
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,
                    int mode, int32_t* labels, int64_t* n_aggs, cudaStream_t st);
 int coarsen_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
