@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
   const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
 
   mis_init_rows<I>(g, a.labels, p, a.T, a.M, a.wl1[0], a.wl2[0], ctr + ctr_c1(0, 0), ctr + ctr_c2(0, 0),
-                   a.warp_degree, a.block_degree, tid, nthreads);
+                   a.warp_degree, a.block_degree);
   int64_t* ts = a.ts;
   if (ts != nullptr && tid == 0) ts[0] = global_ns();  // start of the launch
   if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr)) return;

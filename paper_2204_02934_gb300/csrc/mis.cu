@@ -14,9 +14,7 @@ __global__ void __launch_bounds__(kBlock) k_mis_init(GraphView<I> g, const int32
                                                      uint32_t* T, uint32_t* M, RowLists wl1, RowLists wl2,
                                                      int32_t* c1, int32_t* c2, int32_t warp_degree,
                                                      int32_t block_degree) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  mis_init_rows<I>(g, labels, p, T, M, wl1, wl2, c1, c2, warp_degree, block_degree, t,
-                   (int64_t)gridDim.x * blockDim.x);
+  mis_init_rows<I>(g, labels, p, T, M, wl1, wl2, c1, c2, warp_degree, block_degree);
 }
 
 // Trace words of a phase: W from the three class counts, D by atomics.

@@ -170,23 +170,28 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
   int64_t dacc = 0;
   // the next iteration's vertex and row bounds are loaded while this
   // iteration's gathers are in flight
-  int64_t base = warp_begin * 32;
-  bool an = base + lane < n_in;
+  // contiguous batch ranges per warp: the kept rows leave in long ascending
+  // runs, so the next round's batches still stage as one span
+  const int64_t nbat = ((int64_t)n_in + 31) / 32;
+  const int64_t per = (nbat + warp_stride - 1) / warp_stride;
+  int64_t base = warp_begin * per * 32;
+  const int64_t end = min((int64_t)n_in, (warp_begin + 1) * per * 32);
+  bool an = base + lane < end;
   int32_t vn = 0;
   int64_t sn = 0, en = 0;
   if (an) {
     vn = ld<false>(wl_in + base + lane);
     row_range(g, vn, sn, en);
   }
-  for (; base < n_in; base += warp_stride * 32) {
+  for (; base < end; base += 32) {
     const bool active = an;
     const int32_t v = vn;
     const int64_t s = sn, e = en;
     const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
     int wd;
     const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp, &wd);
-    const int64_t inext = base + warp_stride * 32 + lane;
-    an = inext < n_in;
+    const int64_t inext = base + 32 + lane;
+    an = inext < end;
     if (an) vn = ld<false>(wl_in + inext);
     uint32_t m = kOut;
     if (active) {
@@ -227,23 +232,28 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
   const int lane = lane_id();
   WarpAppender app{stage_warp + kStageWarpWords, wl_out, cnt_out, 0};
   int64_t dacc = 0;
-  int64_t base = warp_begin * 32;
-  bool an = base + lane < n_in;
+  // contiguous batch ranges per warp: the kept rows leave in long ascending
+  // runs, so the next round's batches still stage as one span
+  const int64_t nbat = ((int64_t)n_in + 31) / 32;
+  const int64_t per = (nbat + warp_stride - 1) / warp_stride;
+  int64_t base = warp_begin * per * 32;
+  const int64_t end = min((int64_t)n_in, (warp_begin + 1) * per * 32);
+  bool an = base + lane < end;
   int32_t vn = 0;
   int64_t sn = 0, en = 0;
   if (an) {
     vn = ld<false>(wl_in + base + lane);
     row_range(g, vn, sn, en);
   }
-  for (; base < n_in; base += warp_stride * 32) {
+  for (; base < end; base += 32) {
     const bool active = an;
     const int32_t v = vn;
     const int64_t s = sn, e = en;
     const int len = active && e - s <= kLaneRowMax ? (int)(e - s) : -1;
     int wd;
     const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp, &wd);
-    const int64_t inext = base + warp_stride * 32 + lane;
-    an = inext < n_in;
+    const int64_t inext = base + 32 + lane;
+    an = inext < end;
     if (an) vn = ld<false>(wl_in + inext);
     bool keep = false;
     if (active) {
@@ -442,33 +452,77 @@ __device__ __forceinline__ void decide_block_rows(const GraphView<I>& g, uint32_
 // the others, and both worklists filled per row class (Algorithm 1:
 // worklist1 = worklist2 = all vertices).  labels == null: whole graph;
 // otherwise the subgraph {v : labels[v] == -1}.
+// Each block takes a contiguous vertex range and appends its members of a
+// class as one ascending run (one reservation per block and class), so the
+// lists start as long ascending runs: the passes stage 32 consecutive rows
+// as one span, and keep that order in their outputs.  Every thread of the
+// block must call this.
 template <typename I>
 __device__ __forceinline__ void mis_init_rows(const GraphView<I>& g, const int32_t* labels, const PrioCfg& p,
                                               uint32_t* T, uint32_t* M, RowLists wl1, RowLists wl2,
                                               int32_t* c1, int32_t* c2, int32_t warp_degree,
-                                              int32_t block_degree, int64_t thread_begin,
-                                              int64_t thread_stride) {
-  const int lane = lane_id();
-  for (int64_t base = thread_begin - lane; base < g.n; base += thread_stride) {
-    const int64_t v = base + lane;
-    int cls = -1;
-    if (v < g.n) {
-      const bool member = labels == nullptr || ld<false>(labels + v) == -1;
-      if (member) {
-        int64_t s, e;
-        row_range(g, v, s, e);
-        cls = row_class(e - s, warp_degree, block_degree);
-        T[v] = make_tuple(p, 0u, (uint32_t)v);
-      } else {
-        T[v] = kOut;
-        M[v] = 0u;
-      }
+                                              int32_t block_degree) {
+  __shared__ int sh_scan[40];
+  __shared__ int sh_cnt[kClasses];
+  __shared__ int32_t sh_base1[kClasses], sh_base2[kClasses];
+  const int64_t per = (g.n + gridDim.x - 1) / gridDim.x;
+  const int64_t v0 = min(g.n, (int64_t)blockIdx.x * per), v1 = min(g.n, v0 + per);
+  if (threadIdx.x < kClasses) sh_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  auto class_of = [&](int64_t v) {
+    if (labels != nullptr && ld<false>(labels + v) != -1) return -1;
+    int64_t s, e;
+    row_range(g, v, s, e);
+    return row_class(e - s, warp_degree, block_degree);
+  };
+  int cnt0 = 0, cnt_hi = 0;  // class 0; classes 1 and 2 in 16-bit halves (per thread: < 2^16 vertices)
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const int cls = class_of(v);
+    if (cls >= 0) {
+      T[v] = make_tuple(p, 0u, (uint32_t)v);
+      cnt0 += cls == 0;
+      cnt_hi += cls == 1 ? 1 : (cls == 2 ? 1 << 16 : 0);
+    } else {
+      T[v] = kOut;
+      M[v] = 0u;
     }
-#pragma unroll
-    for (int c = 0; c < kClasses; c++) {
-      warp_append(cls == c, (int32_t)v, wl1.l[c], c1 + c);
-      warp_append(cls == c, (int32_t)v, wl2.l[c], c2 + c);
+  }
+  {
+    const int x0 = __reduce_add_sync(kFull, (unsigned)cnt0);
+    const int x1 = __reduce_add_sync(kFull, (unsigned)(cnt_hi & 0xFFFF));
+    const int x2 = __reduce_add_sync(kFull, (unsigned)(cnt_hi >> 16));
+    if (lane_id() == 0) {
+      if (x0 > 0) atomicAdd(sh_cnt + 0, x0);
+      if (x1 > 0) atomicAdd(sh_cnt + 1, x1);
+      if (x2 > 0) atomicAdd(sh_cnt + 2, x2);
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < kClasses) {
+    const int x = sh_cnt[threadIdx.x];
+    sh_base1[threadIdx.x] = x > 0 ? atomicAdd(c1 + threadIdx.x, x) : 0;
+    sh_base2[threadIdx.x] = x > 0 ? atomicAdd(c2 + threadIdx.x, x) : 0;
+  }
+  __syncthreads();
+  int run0 = 0, run1 = 0, run2 = 0;
+  for (int64_t t0 = v0; t0 < v1; t0 += blockDim.x) {
+    const int64_t v = t0 + threadIdx.x;
+    const int cls = v < v1 ? class_of(v) : -1;
+    // the three class counts of the tile packed in 10-bit fields
+    const int packed = cls < 0 ? 0 : 1 << (10 * cls);
+    int tile_total;
+    const int x = block_exclusive_scan(packed, sh_scan, &tile_total);
+    if (cls >= 0) {
+      const int run = cls == 0 ? run0 : (cls == 1 ? run1 : run2);
+      const int pos = run + ((x >> (10 * cls)) & 1023);
+      int32_t* l1 = cls == 0 ? wl1.l[0] : (cls == 1 ? wl1.l[1] : wl1.l[2]);
+      int32_t* l2 = cls == 0 ? wl2.l[0] : (cls == 1 ? wl2.l[1] : wl2.l[2]);
+      l1[sh_base1[cls] + pos] = (int32_t)v;
+      l2[sh_base2[cls] + pos] = (int32_t)v;
+    }
+    run0 += tile_total & 1023;
+    run1 += (tile_total >> 10) & 1023;
+    run2 += (tile_total >> 20) & 1023;
   }
 }
 
