@@ -190,20 +190,21 @@ __device__ __forceinline__ int warp_inclusive_sum(int x) {
   return x;
 }
 
-// Ascending bitonic sort of 32 * kSmallK keys held lane-major (key index =
-// lane * kSmallK + r).
-__device__ __forceinline__ void warp_sort_keys(uint32_t (&k)[kSmallK]) {
+// Ascending bitonic sort of 32 * K keys held lane-major (key index =
+// lane * K + r), in registers and shuffles.
+template <int K>
+__device__ __forceinline__ void warp_sort_keys(uint32_t (&k)[K]) {
   const int lane = lane_id();
 #pragma unroll
-  for (int size = 2; size <= kSmallEntries; size <<= 1) {
+  for (int size = 2; size <= 32 * K; size <<= 1) {
 #pragma unroll
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      if (stride < kSmallK) {
+      if (stride < K) {
 #pragma unroll
-        for (int r = 0; r < kSmallK; r++) {
+        for (int r = 0; r < K; r++) {
           const int q = r ^ stride;
           if (q > r) {
-            const bool up = (((lane * kSmallK + r) & size) == 0);
+            const bool up = (((lane * K + r) & size) == 0);
             const uint32_t x = k[r], y = k[q];
             const bool sw = (x > y) == up;
             k[r] = sw ? y : x;
@@ -211,12 +212,12 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t (&k)[kSmallK]) {
           }
         }
       } else {
-        const int lx = stride / kSmallK;
+        const int lx = stride / K;
         const bool lower = (lane & lx) == 0;
 #pragma unroll
-        for (int r = 0; r < kSmallK; r++) {
+        for (int r = 0; r < K; r++) {
           const uint32_t o = __shfl_xor_sync(kFull, k[r], lx);
-          const bool up = (((lane * kSmallK + r) & size) == 0);
+          const bool up = (((lane * K + r) & size) == 0);
           k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
         }
       }
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const i
         const int32_t own = (int32_t)A + sel[lj[r]];
         key[r] = (l >= 0 && l != own) ? ((uint32_t)lj[r] << kSmallLabelBits) | (uint32_t)l : 0xFFFFFFFFu;
       }
-      warp_sort_keys(key);
+      warp_sort_keys<kSmallK>(key);
       // distinct keys in order: their index among all distinct keys
       uint32_t prev = __shfl_up_sync(kFull, key[kSmallK - 1], 1);
       if (lane == 0) prev = 0xFFFFFFFFu;
@@ -373,16 +374,16 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
     if (lane == 0) scnt[wib] = 0;
     __syncwarp();
     const int64_t mb = agg_ptr[a], me = agg_ptr[a + 1];
+    bool full = false;
     walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](auto& lab) {
       int32_t prev = -1;
 #pragma unroll
       for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++) {
         const int32_t l = lab[j];
-        if (l < 0 || l == prev) continue;
-        // past the distinct cap the aggregate goes to the bitmap path: stop
-        // inserting (each lane has at most one insert in flight past the cap,
-        // so the table never fills and probing ends)
-        if (*reinterpret_cast<volatile int32_t*>(scnt + wib) > kDistinctCap) break;
+        // past the distinct cap the aggregate goes to the bitmap path: a lane
+        // stops inserting once its own insertion found the cap reached, so
+        // the table holds at most kDistinctCap + 32 labels and probing ends
+        if (l < 0 || l == prev || full) continue;
         prev = l;
         uint32_t h = label_hash(l);
         for (int probe = 0; probe < kHashSlots; probe++) {
@@ -390,6 +391,7 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
           if (old == -1) {
             const int p = atomicAdd(scnt + wib, 1);
             if (p < kDistinctCap) dl[p] = l;
+            else full = true;
             break;
           }
           if (old == l) break;

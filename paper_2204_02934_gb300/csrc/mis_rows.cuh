@@ -145,7 +145,11 @@ __device__ __forceinline__ uint32_t gather_min(const uint32_t* T, const int32_t*
 }
 
 // The decide tests over M[row[k]], k < len (len <= W): any OUT, all equal to
-// t or 0 (masked neighbours of a phase-2 MIS-2).
+// t or 0 (masked neighbours of a phase-2 MIS-2).  Each such M is OUT, 0 or
+// at most t = T_v (v lies in every neighbour's closed neighbourhood, whose
+// minimum M is, and T_v has not changed since), so "any OUT" is max == OUT
+// and, when there is none, "all t or 0" is min(M - 1) >= t - 1 (0 wraps to
+// the largest value).  t >= 1 for an undecided vertex.
 template <int W, bool NC, typename F>
 __device__ __forceinline__ void gather_decide(const uint32_t* M, const int32_t* row, int len, uint32_t t,
                                               bool& any_out, bool& all_eq, F&& between) {
@@ -153,11 +157,14 @@ __device__ __forceinline__ void gather_decide(const uint32_t* M, const int32_t* 
 #pragma unroll
   for (int k = 0; k < W; k++) mw[k] = k < len ? ld<NC>(M + row[k]) : t;
   between();
+  uint32_t mx = 0u, mn = ~0u;
 #pragma unroll
   for (int k = 0; k < W; k++) {
-    any_out |= mw[k] == kOut;
-    all_eq &= (mw[k] == t) | (mw[k] == 0u);
+    mx = max(mx, mw[k]);
+    mn = min(mn, mw[k] - 1u);
   }
+  any_out |= mx == kOut;
+  all_eq &= mn >= t - 1u;
 }
 
 template <typename I, bool NC>
