@@ -87,7 +87,7 @@ typedef struct {
   int32_t block_degree;   /* rows with degree >= this get a full block (default 2048) */
   int32_t block_size;     /* threads per block for row kernels (default 256) */
   int32_t loop;           /* MIS2_LOOP_*; default DEVICE */
-  int32_t debug_checks;   /* validate CSR and roots (extra passes); default 0 */
+  int32_t debug_checks;   /* MIS2_DEBUG_* bits (extra passes, synchronising); default 0 */
   int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
   int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = default (2) */
   int64_t spin_limit;     /* polls before a device barrier reports MIS2_ERR_TIMEOUT */
@@ -97,6 +97,21 @@ typedef struct {
  * mis2_coarsen_level on a context.  trace[r] = {W1, W2, D1, D2}: worklist
  * sizes and summed row lengths at the start of MIS-2 round r (phase-1 MIS-2
  * in trace, phase-2 MIS-2 in trace2), up to MIS2_TRACE_CAP rounds. */
+/* debug_checks bits.
+ * MIS2_DEBUG_VALIDATE: before computing, every entry point taking a graph
+ *   checks rowptr (0 first, nnz last, non-decreasing), colind in [0, n) and
+ *   symmetry (two order-independent 64-bit hash sums over the entries and
+ *   over their mirrors must agree); mis2_aggregate also checks that the roots
+ *   are ascending, in range and pairwise more than two hops apart, and
+ *   mis2_coarsen that every label is in [0, n_aggs).  A failed check returns
+ *   MIS2_ERR_BAD_GRAPH before any kernel indexes memory with the bad value.
+ * MIS2_DEBUG_FORCE_TIMEOUT: test hook for the bounded waits: the device
+ *   loop's grid barriers wait for one arrival more than the grid makes, so
+ *   every block gives up after spin_limit polls and the call returns
+ *   MIS2_ERR_TIMEOUT; the context stays usable. */
+#define MIS2_DEBUG_VALIDATE 0x1
+#define MIS2_DEBUG_FORCE_TIMEOUT 0x100
+
 #define MIS2_TRACE_CAP 64
 #define MIS2_LOOP_TS_WORDS (4 + 4 * MIS2_TRACE_CAP)
 #define MIS2_NUM_KERNEL_CLASSES 8

@@ -178,6 +178,12 @@ static int alloc_scratch(mis2_ctx* c) {
   return MIS2_OK;
 }
 
+// Debug-mode validation of a graph argument (MIS2_DEBUG_VALIDATE).
+static int debug_graph(mis2_ctx* c, const GraphArgs& ga, cudaStream_t st) {
+  if (!(c->cfg.debug_checks & MIS2_DEBUG_VALIDATE)) return MIS2_OK;
+  return check_graph(c, ga, st);
+}
+
 static void begin_call(mis2_ctx* c) {
   c->launches = 0;
   memset(c->stats.loop_ns, 0, sizeof(c->stats.loop_ns));
@@ -301,6 +307,7 @@ int mis2_run(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int
   MIS2_TRY(validate_graph(c, g, &ga));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
   int rc = run_impl(c, ga, make_prio(c, ga.n, seed), in_set, roots, n_roots, n_rounds, st);
   if (rc == MIS2_OK) rc = timer_collect(c);
   return rc;
@@ -314,6 +321,7 @@ int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* pri
   MIS2_TRY(validate_graph(c, g, &ga));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
   PrioCfg p = make_prio(c, ga.n, 0);
   uint32_t* dtab = nullptr;
   const size_t bytes = (size_t)table_rounds * (size_t)ga.n * sizeof(uint32_t);
@@ -346,6 +354,8 @@ int mis2_aggregate(mis2_ctx* c, const mis2_csr* g, const int32_t* roots, int64_t
     return MIS2_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
+  if (c->cfg.debug_checks & MIS2_DEBUG_VALIDATE) MIS2_TRY(check_roots(c, ga, roots, n_roots, st));
   int rc = aggregate_impl(c, ga, roots, n_roots, seed, mode, labels, n_aggs, st);
   if (rc == MIS2_OK) rc = fetch_trace(c, 1, c->stats.rounds2, st);
   if (rc == MIS2_OK) {
@@ -366,6 +376,8 @@ int mis2_coarsen(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t 
     return MIS2_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
+  if (c->cfg.debug_checks & MIS2_DEBUG_VALIDATE) MIS2_TRY(check_labels(c, labels, ga.n, n_aggs, st));
   int rc = coarsen_impl(c, ga, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, c_nnz, st);
   if (rc == MIS2_OK) {
     c->stats.c_nnz = *c_nnz;
@@ -463,6 +475,7 @@ int mis2_coarsen_level(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* i
     return MIS2_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
   int rc = level_impl(c, ga, seed, in_set, roots, labels, c_rowptr, c_colind, c_colind_cap, n_roots, n_aggs, c_nnz,
                       st);
   if (rc == MIS2_OK) rc = timer_collect(c);
@@ -507,6 +520,7 @@ int mis2_coarsen_level_host(mis2_ctx* c, const mis2_csr* gh, uint64_t seed, uint
   gd.colind = h.colind;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, &gd, &ga));
+  MIS2_TRY(debug_graph(c, ga, st));
   int64_t nr = 0, na = 0, cn = 0;
   MIS2_TRY(level_impl(c, ga, seed, h.in_set, h.roots, h.labels, c_rowptr ? h.c_rowptr : nullptr, h.c_colind,
                       c->max_nnz, &nr, &na, &cn, st));

@@ -42,7 +42,7 @@ __device__ __forceinline__ int64_t global_ns() {
 // ts (optional): ts[0] = latest arrival time, ts[1] = block 0's departure
 // time (globaltimer, ns).
 __device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t& epoch, int32_t* err, int64_t spin_limit,
-                                             int64_t* ts = nullptr) {
+                                             int64_t* ts = nullptr, int32_t extra = 0) {
   __shared__ int ok;
   __syncthreads();
   epoch++;
@@ -51,7 +51,7 @@ __device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t& epoch, int
     if (ts != nullptr) atomicMax(reinterpret_cast<unsigned long long*>(ts), (unsigned long long)global_ns());
     __threadfence();
     atomicAdd(count, 1);
-    const uint32_t target = (uint32_t)epoch * gridDim.x;
+    const uint32_t target = (uint32_t)epoch * gridDim.x + (uint32_t)extra;
     int64_t spins = 0;
     while ((int32_t)((uint32_t)ld_acquire_i32(count) - target) < 0) {
       if (++spins > spin_limit || (ld_volatile_i32(err) & kErrTimeout)) {
@@ -82,6 +82,8 @@ struct LoopArgs {
   int32_t block_degree;
   int32_t max_rounds;
   int32_t rounds_slot;
+  int32_t barrier_extra;  // arrivals awaited beyond the grid: 1 = forced timeout (test hook)
+  int32_t pad;
 };
 
 template <int G, typename I>
@@ -102,7 +104,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
                    a.warp_degree, a.block_degree);
   int64_t* ts = a.ts;
   if (ts != nullptr && tid == 0) ts[0] = global_ns();  // start of the launch
-  if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr)) return;
+  if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr, a.barrier_extra)) return;
 
   int r = 0;
   for (;; r++) {
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
       column_block_rows<I, false>(g, a.T, a.M, in2.l[2], n2[2], out2.l[2], ctr + ctr_c2(nslot, 2), d2, blockIdx.x,
                                   gridDim.x, sh);
     const bool ts_on = ts != nullptr && r < MIS2_TRACE_CAP;
-    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr)) return;
+    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr, a.barrier_extra)) return;
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = w1;
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     if (n1[2] > 0)
       decide_block_rows<I, false>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
                                   (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
-    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr)) return;
+    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr, a.barrier_extra)) return;
   }
   if (tid == 0) ctr[a.rounds_slot] = r;
 }
@@ -219,6 +221,8 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.block_degree = c->cfg.block_degree;
   la.max_rounds = (int32_t)std::min<int64_t>(g.n, (int64_t)1 << 30);
   la.rounds_slot = rounds_slot;
+  la.barrier_extra = (c->cfg.debug_checks & MIS2_DEBUG_FORCE_TIMEOUT) ? 1 : 0;
+  la.pad = 0;
   if (sync) {
     MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
   } else {

@@ -34,6 +34,7 @@ enum : int {
   kCtrRounds2 = 32,  // rounds of the phase-2 device loop
   kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch
   kCtrGiant = 34,    // giant member rows of the current bitmap batch
+  kCtrCheckSums = 36,  // debug checks: two 64-bit entry-hash sums (words 36-39)
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 40;
@@ -48,7 +49,8 @@ enum : int {
   kErrNoAggregatedNeighbour = 2,
   kErrNoProgress = 4,
   kErrCapacity = 8,
-  kErrLargeOverflow = 16
+  kErrLargeOverflow = 16,
+  kErrBadGraph = 32  // debug checks: malformed or asymmetric CSR, roots not distance-2 independent
 };
 constexpr int kLoopTsWords = MIS2_LOOP_TS_WORDS;
 
@@ -213,6 +215,12 @@ int agg_level_async(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const
 int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                  int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st);
 bool coarsen_fast_needs_retry(const mis2_ctx* c);
+// Debug-mode validation (synchronises): MIS2_ERR_BAD_GRAPH for a malformed or
+// asymmetric CSR, or for roots that are not ascending and pairwise more than
+// two hops apart.
+int check_graph(mis2_ctx* c, const GraphArgs& g, cudaStream_t st);
+int check_roots(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, cudaStream_t st);
+int check_labels(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, cudaStream_t st);
 int coarsen_fast_finish(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                         int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st);
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,

@@ -56,3 +56,11 @@ def test_struct_sizes_match_header():
 def test_null_context_is_rejected(lib):
     nr = ctypes.c_int64(0)
     assert lib.mis2_run(None, None, 0, None, None, ctypes.byref(nr), None, None) == -1
+
+
+def test_debug_bits_match_the_header():
+    hdr = open(os.path.join(ROOT, "include", "mis2.h")).read()
+    for name in ("MIS2_DEBUG_VALIDATE", "MIS2_DEBUG_FORCE_TIMEOUT"):
+        m = re.search(r"#define\s+" + name + r"\s+(0x[0-9a-fA-F]+|\d+)", hdr)
+        assert m, name
+        assert int(m.group(1), 0) == getattr(mis2, name)
