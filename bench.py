@@ -6,7 +6,7 @@ MIS-2 (Algorithm 1), aggregation (Algorithm 3) and the coarse graph.  The
 metric is edges/s = input entries per step / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 27pt|small|rmat|serve]
+                  [--workload 27pt|small|rmat|serve|ablation]
 
 - value: device-resident input, CUDA events around each step, L2 flushed
   (256 MiB write) before every step, outside the timed interval.
@@ -488,6 +488,61 @@ def run_serve(args):
     return 0
 
 
+def run_ablation(args):
+    """Fig. 2 / Table I on GB300: MIS-2 (Algorithm 1) alone on the regenerated
+    Laplace3D_100 (7-point 100^3) and Elasticity3D_60 (27-point x 3 dof
+    60^3), with each optimisation switched off in turn: worklists, random
+    (xorshift*) priorities -> fixed priorities or plain xorshift.  Device
+    loop, input resident, L2 flushed before each timed run."""
+    import torch
+
+    from paper_2204_02934_gb300 import _build, graphgen as gg, mis2
+
+    _build.build()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    variants = [("all optimisations", {}),
+                ("no worklists", {"ablation": mis2.MIS2_ABLATE_NO_WORKLISTS}),
+                ("fixed priorities (no random tie-break per round)", {"hash_variant": mis2.MIS2_HASH_FIXED}),
+                ("xorshift instead of xorshift*", {"hash_variant": mis2.MIS2_HASH_XORSHIFT})]
+    graphs = [("Laplace3D_100 (7-point 100^3)", gg.grid3d_7pt(100, 100, 100)),
+              ("Elasticity3D_60 (27-point x 3 dof, 60^3)", gg.elasticity3d(60, 60, 60))]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for gname, g in graphs:
+        dg = mis2.DeviceGraph.from_host(g)
+        ref = None
+        for vname, over in variants:
+            ctx = mis2.Context(g.n, g.nnz, loop=mis2.MIS2_LOOP_DEVICE if args.loop == "device" else
+                               mis2.MIS2_LOOP_HOST, **over)
+            for _ in range(max(args.warmup, 3)):
+                in_set, roots, rounds = ctx.run(dg, 0)
+            times = []
+            for _ in range(args.steps):
+                flush.fill_(1)
+                ev0.record()
+                in_set, roots, rounds = ctx.run(dg, 0)
+                ev1.record()
+                ev1.synchronize()
+                times.append(ev0.elapsed_time(ev1))
+            if ref is None:
+                ref = in_set.clone()
+            same = bool(torch.equal(in_set, ref)) if "worklists" in vname else None
+            rows.append({"graph": gname, "n": g.n, "nnz": g.nnz, "variant": vname, "rounds": int(rounds),
+                         "mis2_size": int(roots.numel()), "ms": round(float(np.median(times)), 4),
+                         "same_result_as_all": same})
+            ctx.close()
+    base = {r["graph"]: r["ms"] for r in rows if r["variant"] == "all optimisations"}
+    for r in rows:
+        r["slowdown_vs_all"] = round(r["ms"] / base[r["graph"]], 3)
+    line = {"metric": "MIS-2 time per variant (Fig. 2 ablation, Table I rounds) on GB300", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "Laplace3D_100 and Elasticity3D_60 regenerated from their definitions, seed 0",
+                       "loop": args.loop, "steps": args.steps},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _traffic_from_profile(kernel):
     """dram bytes per launch recorded by an ncu capture of this kernel, when
     the recorded source digest still matches the library sources."""
@@ -515,7 +570,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat", "serve"])
+    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat", "serve", "ablation"])
     ap.add_argument("--loop", default="device", choices=["device", "host"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
@@ -527,6 +582,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -90,6 +90,8 @@ typedef struct {
   int32_t debug_checks;   /* MIS2_DEBUG_* bits (extra passes, synchronising); default 0 */
   int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
   int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = default (2) */
+  int32_t ablation;       /* MIS2_ABLATE_* bits (the Fig. 2 variants); default 0 */
+  int32_t reserved;       /* 0 */
   int64_t spin_limit;     /* polls before a device barrier reports MIS2_ERR_TIMEOUT */
 } mis2_config;
 
@@ -109,6 +111,14 @@ typedef struct {
  *   loop's grid barriers wait for one arrival more than the grid makes, so
  *   every block gives up after spin_limit polls and the call returns
  *   MIS2_ERR_TIMEOUT; the context stays usable. */
+/* ablation bits (Section VI-A, Fig. 2: the optimisations one at a time).
+ * MIS2_ABLATE_NO_WORKLISTS: every round visits every vertex of the
+ *   (sub)graph in both steps instead of the compacted worklists (decide skips
+ *   vertices already IN or OUT); the result is the same MIS-2.  The fixed
+ *   priorities and the xorshift hash of Fig. 2 / Table I are hash_variant
+ *   values.  Per-round statistics then count the vertices visited. */
+#define MIS2_ABLATE_NO_WORKLISTS 0x1
+
 #define MIS2_DEBUG_VALIDATE 0x1
 #define MIS2_DEBUG_FORCE_TIMEOUT 0x100
 

@@ -86,6 +86,7 @@ static int validate_cfg(const mis2_config* cfg) {
   if (cfg->block_size != kBlock) return MIS2_ERR_INVALID_ARG;
   if (cfg->loop != MIS2_LOOP_HOST && cfg->loop != MIS2_LOOP_DEVICE) return MIS2_ERR_INVALID_ARG;
   if (cfg->spin_limit < 1 || cfg->loop_blocks_per_sm < 0) return MIS2_ERR_INVALID_ARG;
+  if ((cfg->ablation & ~MIS2_ABLATE_NO_WORKLISTS) != 0 || cfg->reserved != 0) return MIS2_ERR_INVALID_ARG;
   return MIS2_OK;
 }
 

@@ -213,7 +213,7 @@ __device__ __forceinline__ void warp_append(bool want, int32_t v, int32_t* list,
   int base = 0;
   if (lane == leader) base = atomicAdd(cnt, __popc(b));
   base = __shfl_sync(kFull, base, leader);
-  if (want) list[base + __popc(b & ((1u << lane) - 1u))] = v;
+  if (want && list != nullptr) list[base + __popc(b & ((1u << lane) - 1u))] = v;
 }
 
 // Add x over the warp into *acc with one 64-bit atomic (acc may be null).

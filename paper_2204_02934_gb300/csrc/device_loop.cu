@@ -83,13 +83,14 @@ struct LoopArgs {
   int32_t max_rounds;
   int32_t rounds_slot;
   int32_t barrier_extra;  // arrivals awaited beyond the grid: 1 = forced timeout (test hook)
-  int32_t pad;
+  int32_t no_worklists;   // visit every vertex every round (ablation)
 };
 
-template <int G, typename I>
+template <int G, typename I, bool NOWL>
 __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
   __shared__ uint32_t sh[40];
   __shared__ int32_t sh_n[2 * kClasses];
+  __shared__ int32_t sh_n0[2 * kClasses];  // round-0 sizes: every vertex (no-worklist mode)
   __shared__ __align__(16) int32_t stage[kBlock / 32][kWarpSmemWords];
   int32_t* my_stage = stage[threadIdx.x >> 5];
   int32_t* ctr = a.ctr;
@@ -106,14 +107,19 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
   if (ts != nullptr && tid == 0) ts[0] = global_ns();  // start of the launch
   if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr, a.barrier_extra)) return;
 
+  constexpr bool nowl = NOWL;
+  const RowLists none{{nullptr, nullptr, nullptr}};
   int r = 0;
   for (;; r++) {
     const int slot = r % 3, nslot = (r + 1) % 3, zslot = (r + 2) % 3;
     // the worklist sizes: read once per block (one request instead of one
     // per warp on the same L2 line) and shared
-    if (threadIdx.x < 2 * kClasses)
-      sh_n[threadIdx.x] = ld_volatile_i32(ctr + (threadIdx.x < kClasses ? ctr_c1(slot, (int)threadIdx.x)
-                                                                         : ctr_c2(slot, (int)threadIdx.x - kClasses)));
+    if (threadIdx.x < 2 * kClasses) {
+      const int32_t x = ld_volatile_i32(ctr + (threadIdx.x < kClasses ? ctr_c1(slot, (int)threadIdx.x)
+                                                                       : ctr_c2(slot, (int)threadIdx.x - kClasses)));
+      sh_n[threadIdx.x] = x;
+      if (r == 0) sh_n0[threadIdx.x] = x;
+    }
     __syncthreads();
     int n1[kClasses], n2[kClasses];
     int w1 = 0, w2 = 0;
@@ -125,6 +131,15 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
       w2 += n2[k];
     }
     if (w1 == 0) break;
+    if (nowl) {  // every vertex visited; n1/n2 above were the compacted counts
+      w2 = 0;
+#pragma unroll
+      for (int k = 0; k < kClasses; k++) {
+        n1[k] = sh_n0[k];
+        n2[k] = sh_n0[kClasses + k];
+        w2 += n2[k];
+      }
+    }
     if (r > a.max_rounds) {
       if (tid == 0) atomicOr(err, kErrNoProgress);
       break;
@@ -132,8 +147,8 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     const bool tr_on = a.dtr != nullptr && r < MIS2_TRACE_CAP;
     int64_t* d2 = tr_on ? a.dtr + r * 4 + 3 : nullptr;
     int64_t* d1 = tr_on ? a.dtr + r * 4 + 2 : nullptr;
-    const RowLists in2 = a.wl2[r & 1], out2 = a.wl2[(r + 1) & 1];
-    const RowLists in1 = a.wl1[r & 1], out1 = a.wl1[(r + 1) & 1];
+    const RowLists in2 = nowl ? a.wl2[0] : a.wl2[r & 1], out2 = nowl ? none : a.wl2[(r + 1) & 1];
+    const RowLists in1 = nowl ? a.wl1[0] : a.wl1[r & 1], out1 = nowl ? none : a.wl1[(r + 1) & 1];
     // ---- column step
     if (tid < kClasses) ctr[ctr_c1(nslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 1] = w2;
@@ -153,18 +168,18 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr, a.barrier_extra)) return;
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
-    if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = w1;
+    if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = nowl ? n1[0] + n1[1] + n1[2] : w1;
     if constexpr (G == 1)
-      decide_lane_rows<I, false>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
+      decide_lane_rows<I, false, NOWL>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
                                  (uint32_t)(r + 1), warp, nwarps, my_stage);
     else
-      decide_group_rows<G, I, false>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
+      decide_group_rows<G, I, false, NOWL>(g, a.T, a.M, in1.l[0], n1[0], out1.l[0], ctr + ctr_c1(nslot, 0), d1, p,
                                      (uint32_t)(r + 1), warp, nwarps);
     if (n1[1] > 0)
-      decide_group_rows<32, I, false>(g, a.T, a.M, in1.l[1], n1[1], out1.l[1], ctr + ctr_c1(nslot, 1), d1, p,
+      decide_group_rows<32, I, false, NOWL>(g, a.T, a.M, in1.l[1], n1[1], out1.l[1], ctr + ctr_c1(nslot, 1), d1, p,
                                       (uint32_t)(r + 1), warp, nwarps);
     if (n1[2] > 0)
-      decide_block_rows<I, false>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
+      decide_block_rows<I, false, NOWL>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
                                   (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
     if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr, a.barrier_extra)) return;
   }
@@ -173,7 +188,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
 
 template <int G, typename I>
 static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cudaStream_t st) {
-  auto kern = k_mis_loop<G, I>;
+  auto kern = la.no_worklists ? k_mis_loop<G, I, true> : k_mis_loop<G, I, false>;
   int per_sm = 0;
   MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
   if (per_sm < 1) return MIS2_ERR_CUDA;
@@ -222,7 +237,7 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.max_rounds = (int32_t)std::min<int64_t>(g.n, (int64_t)1 << 30);
   la.rounds_slot = rounds_slot;
   la.barrier_extra = (c->cfg.debug_checks & MIS2_DEBUG_FORCE_TIMEOUT) ? 1 : 0;
-  la.pad = 0;
+  la.no_worklists = (c->cfg.ablation & MIS2_ABLATE_NO_WORKLISTS) ? 1 : 0;
   if (sync) {
     MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
   } else {

@@ -35,6 +35,7 @@ enum : int {
   kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch
   kCtrGiant = 34,    // giant member rows of the current bitmap batch
   kCtrCheckSums = 36,  // debug checks: two 64-bit entry-hash sums (words 36-39)
+  kCtrInitSizes = 40,  // no-worklist mode of the host loop: round-0 list sizes (words 40-45)
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 40;

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kBlock) k_column(GraphView<I> g, const uint32_
                                 nw);
 }
 
-template <int G, typename I>
+template <int G, typename I, bool GUARD>
 __global__ void __launch_bounds__(kBlock) k_decide(GraphView<I> g, uint32_t* T, const uint32_t* M,
                                                    const int32_t* wl_in, const int32_t* cnt_in,
                                                    int32_t* wl_out, int32_t* cnt_out, int32_t* zero,
@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(kBlock) k_decide(GraphView<I> g, uint32_t* T, 
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  decide_group_rows<G, I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, p, next_iter, warp,
-                                nw);
+  decide_group_rows<G, I, true, GUARD>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, p, next_iter,
+                                       warp, nw);
 }
 
 template <typename I>
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kBlock) k_column_lane(GraphView<I> g, const ui
                             stage[threadIdx.x >> 5]);
 }
 
-template <typename I>
+template <typename I, bool GUARD>
 __global__ void __launch_bounds__(kBlock) k_decide_lane(GraphView<I> g, uint32_t* T, const uint32_t* M,
                                                         const int32_t* wl_in, const int32_t* cnt_in, int32_t* wl_out,
                                                         int32_t* cnt_out, int32_t* zero, PhaseTrace tr, PrioCfg p,
@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(kBlock) k_decide_lane(GraphView<I> g, uint32_t
   phase_prologue(zero, tr);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  decide_lane_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, p, next_iter, warp, nw,
-                            stage[threadIdx.x >> 5]);
+  decide_lane_rows<I, true, GUARD>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, tr.d, p, next_iter, warp,
+                                   nw, stage[threadIdx.x >> 5]);
 }
 
 template <typename I>
@@ -87,14 +87,14 @@ __global__ void __launch_bounds__(kBlock) k_column_block(GraphView<I> g, const u
   column_block_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, dsum, blockIdx.x, gridDim.x, sh);
 }
 
-template <typename I>
+template <typename I, bool GUARD>
 __global__ void __launch_bounds__(kBlock) k_decide_block(GraphView<I> g, uint32_t* T, const uint32_t* M,
                                                          const int32_t* wl_in, const int32_t* cnt_in,
                                                          int32_t* wl_out, int32_t* cnt_out, int64_t* dsum,
                                                          PrioCfg p, uint32_t next_iter) {
   __shared__ uint32_t sh[40];
-  decide_block_rows<I, true>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, dsum, p, next_iter, blockIdx.x,
-                             gridDim.x, sh);
+  decide_block_rows<I, true, GUARD>(g, T, M, wl_in, block_load(cnt_in), wl_out, cnt_out, dsum, p, next_iter,
+                                    blockIdx.x, gridDim.x, sh);
 }
 
 __global__ void __launch_bounds__(1024) k_scan_tile_counts(int32_t* tile_cnt, int64_t ntiles, int32_t* total) {
@@ -223,21 +223,33 @@ static void launch_column(mis2_ctx* c, const GraphView<I>& gv, int G, int cls, i
 template <typename I>
 static void launch_decide(mis2_ctx* c, const GraphView<I>& gv, int G, int cls, int blocks, const int32_t* wl_in,
                           const int32_t* cnt_in, int32_t* wl_out, int32_t* cnt_out, int32_t* zero,
-                          PhaseTrace tr, const PrioCfg& p, uint32_t next_iter, cudaStream_t st) {
+                          PhaseTrace tr, const PrioCfg& p, uint32_t next_iter, cudaStream_t st, bool guard) {
   c->launches++;
   if (cls == 2) {
-    k_decide_block<I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, tr.d, p,
-                                                 next_iter);
+    if (guard)
+      k_decide_block<I, true><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, tr.d,
+                                                         p, next_iter);
+    else
+      k_decide_block<I, false><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, tr.d,
+                                                          p, next_iter);
     return;
   }
   if (cls == 1) G = 32;
 #define MIS2_DEC(GG)                                                                                      \
-  k_decide<GG, I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, tr, \
-                                             p, next_iter)
+  if (guard)                                                                                              \
+    k_decide<GG, I, true><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, \
+                                                     tr, p, next_iter);                                        \
+  else                                                                                                    \
+    k_decide<GG, I, false><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, \
+                                                      tr, p, next_iter)
   switch (G) {
     case 1:
-      k_decide_lane<I><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero, tr, p,
-                                                  next_iter);
+      if (guard)
+        k_decide_lane<I, true><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero,
+                                                          tr, p, next_iter);
+      else
+        k_decide_lane<I, false><<<blocks, kBlock, 0, st>>>(gv, c->s.T, c->s.M, wl_in, cnt_in, wl_out, cnt_out, zero,
+                                                           tr, p, next_iter);
       break;
     case 2: MIS2_DEC(2); break;
     case 4: MIS2_DEC(4); break;
@@ -269,8 +281,22 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
   c->launches++;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
+  // no-worklist mode (ablation): every round visits the round-0 lists, whose
+  // sizes are kept in ctr words kCtrInitSizes.. (the slots rotate)
+  const bool nowl = (c->cfg.ablation & MIS2_ABLATE_NO_WORKLISTS) != 0;
+  if (nowl) {
+    MIS2_CUDA(cudaMemcpyAsync(s.ctr + kCtrInitSizes, s.ctr + ctr_c1(0, 0), kClasses * sizeof(int32_t),
+                              cudaMemcpyDeviceToDevice, st));
+    MIS2_CUDA(cudaMemcpyAsync(s.ctr + kCtrInitSizes + kClasses, s.ctr + ctr_c2(0, 0), kClasses * sizeof(int32_t),
+                              cudaMemcpyDeviceToDevice, st));
+  }
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MIS2_CUDA(cudaStreamSynchronize(st));
+  int32_t n1_0[kClasses], n2_0[kClasses];
+  for (int k = 0; k < kClasses; k++) {
+    n1_0[k] = c->h_ctr[ctr_c1(0, k)];
+    n2_0[k] = c->h_ctr[ctr_c2(0, k)];
+  }
   int r = 0;
   for (;;) {
     const int slot = r % 3, nslot = (r + 1) % 3, zslot = (r + 2) % 3;
@@ -283,12 +309,17 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
     }
     if (w1 == 0) break;
     if (r > g.n) return MIS2_ERR_NO_PROGRESS;
+    if (nowl)
+      for (int k = 0; k < kClasses; k++) {
+        n1[k] = n1_0[k];
+        n2[k] = n2_0[k];
+      }
     const bool tr_on = r < MIS2_TRACE_CAP;
-    PhaseTrace tcol{tr_on ? dtr + r * 4 + 1 : nullptr, tr_on ? dtr + r * 4 + 3 : nullptr,
-                    s.ctr + ctr_c2(slot, 0)};
-    PhaseTrace tdec{tr_on ? dtr + r * 4 + 0 : nullptr, tr_on ? dtr + r * 4 + 2 : nullptr,
-                    s.ctr + ctr_c1(slot, 0)};
-    const int rp = r & 1, wp = (r + 1) & 1;
+    int32_t* c1_in = nowl ? s.ctr + kCtrInitSizes : s.ctr + ctr_c1(slot, 0);
+    int32_t* c2_in = nowl ? s.ctr + kCtrInitSizes + kClasses : s.ctr + ctr_c2(slot, 0);
+    PhaseTrace tcol{tr_on ? dtr + r * 4 + 1 : nullptr, tr_on ? dtr + r * 4 + 3 : nullptr, c2_in};
+    PhaseTrace tdec{tr_on ? dtr + r * 4 + 0 : nullptr, tr_on ? dtr + r * 4 + 2 : nullptr, c1_in};
+    const int rp = nowl ? 0 : r & 1, wp = (r + 1) & 1;
     // column step over worklist2
     timer_begin(c, kKcColumn, st);
     for (int k = 0; k < kClasses; k++) {
@@ -297,7 +328,7 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
       const int blocks = grid_for(c, n2[k], per_block, k == 2 ? 4 : 8);
       PhaseTrace t = tcol;
       if (k > 0) t.w = nullptr;
-      launch_column<I>(c, gv, G, k, blocks, s.wl2[rp][k], s.ctr + ctr_c2(slot, k), s.wl2[wp][k],
+      launch_column<I>(c, gv, G, k, blocks, s.wl2[rp][k], c2_in + k, nowl ? nullptr : s.wl2[wp][k],
                        s.ctr + ctr_c2(nslot, k), k == 0 ? s.ctr + ctr_c1(nslot, 0) : nullptr, t, st);
     }
     timer_end(c, st);
@@ -309,9 +340,9 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
       const int blocks = grid_for(c, n1[k], per_block, k == 2 ? 4 : 8);
       PhaseTrace t = tdec;
       if (k > 0) t.w = nullptr;
-      launch_decide<I>(c, gv, G, k, blocks, s.wl1[rp][k], s.ctr + ctr_c1(slot, k), s.wl1[wp][k],
+      launch_decide<I>(c, gv, G, k, blocks, s.wl1[rp][k], c1_in + k, nowl ? nullptr : s.wl1[wp][k],
                        s.ctr + ctr_c1(nslot, k), k == 0 ? s.ctr + ctr_c2(zslot, 0) : nullptr, t, p,
-                       (uint32_t)(r + 1), st);
+                       (uint32_t)(r + 1), st, nowl);
     }
     timer_end(c, st);
     MIS2_CUDA(cudaGetLastError());

@@ -54,7 +54,8 @@ struct WarpAppender {
     int base = 0;
     if (lane == 0) base = atomicAdd(cnt, n);
     base = __shfl_sync(kFull, base, 0);
-    for (int i = lane; i < n; i += 32) list[base + i] = buf[i];
+    if (list != nullptr)  // null list: count only
+      for (int i = lane; i < n; i += 32) list[base + i] = buf[i];
     __syncwarp();
     n = 0;
   }
@@ -231,7 +232,7 @@ __device__ __forceinline__ void column_lane_rows(const GraphView<I>& g, const ui
   if (dsum != nullptr) warp_accumulate(dacc, dsum);
 }
 
-template <typename I, bool NC>
+template <typename I, bool NC, bool GUARD = false>
 __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t* T, const uint32_t* M,
                                                  const int32_t* wl_in, int n_in, int32_t* wl_out, int32_t* cnt_out,
                                                  int64_t* dsum, const PrioCfg& p, uint32_t next_iter,
@@ -246,11 +247,18 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
   int64_t base = warp_begin * per * 32;
   const int64_t end = min((int64_t)n_in, (warp_begin + 1) * per * 32);
   bool an = base + lane < end;
+  // GUARD (visiting every vertex, no worklists): vertices already IN or OUT
+  // are skipped before their rows are read
+  auto undecided = [&](int32_t x) {
+    const uint32_t tv = ld<false>(T + x);
+    return tv != kIn && tv != kOut;
+  };
   int32_t vn = 0;
   int64_t sn = 0, en = 0;
   if (an) {
     vn = ld<false>(wl_in + base + lane);
-    row_range(g, vn, sn, en);
+    if (GUARD) an = undecided(vn);
+    if (an) row_range(g, vn, sn, en);
   }
   for (; base < end; base += 32) {
     const bool active = an;
@@ -262,6 +270,7 @@ __device__ __forceinline__ void decide_lane_rows(const GraphView<I>& g, uint32_t
     const int64_t inext = base + 32 + lane;
     an = inext < end;
     if (an) vn = ld<false>(wl_in + inext);
+    if (GUARD && an) an = undecided(vn);
     bool keep = false;
     if (active) {
       const uint32_t t = ld<false>(T + v);
@@ -338,7 +347,7 @@ __device__ __forceinline__ void column_group_rows(const GraphView<I>& g, const u
   if (dsum != nullptr) warp_accumulate(dacc, dsum);
 }
 
-template <int G, typename I, bool NC>
+template <int G, typename I, bool NC, bool GUARD = false>
 __device__ __forceinline__ void decide_group_rows(const GraphView<I>& g, uint32_t* T, const uint32_t* M,
                                                   const int32_t* wl_in, int n_in, int32_t* wl_out,
                                                   int32_t* cnt_out, int64_t* dsum, const PrioCfg& p,
@@ -349,17 +358,20 @@ __device__ __forceinline__ void decide_group_rows(const GraphView<I>& g, uint32_
   int64_t dacc = 0;
   for (int64_t base = warp_begin * RPW; base < n_in; base += warp_stride * RPW) {
     const int64_t i = base + sub;
-    const bool active = i < n_in;
+    bool active = i < n_in;
     int32_t v = 0;
     uint32_t t = 0;
     bool any_out = false, all_eq = true;
     int64_t len = 0;
     if (active) {
       v = ld<false>(wl_in + i);
+      t = ld<false>(T + v);
+      if (GUARD && (t == kIn || t == kOut)) active = false;
+    }
+    if (active) {
       int64_t s, e;
       row_range(g, v, s, e);
       len = e - s;
-      t = ld<false>(T + v);
       const uint32_t mv = ld<NC>(M + v);
       any_out = mv == kOut;
       all_eq = mv == t;
@@ -406,13 +418,16 @@ __device__ __forceinline__ void column_block_rows(const GraphView<I>& g, const u
     if (threadIdx.x == 0) {
       if (m == kIn) m = kOut;
       M[v] = m;
-      if (m != kOut) wl_out[atomicAdd(cnt_out, 1)] = v;
+      if (m != kOut) {
+        const int32_t pos = atomicAdd(cnt_out, 1);
+        if (wl_out != nullptr) wl_out[pos] = v;
+      }
       if (dsum != nullptr) atomicAdd(reinterpret_cast<unsigned long long*>(dsum), (unsigned long long)(e - s));
     }
   }
 }
 
-template <typename I, bool NC>
+template <typename I, bool NC, bool GUARD = false>
 __device__ __forceinline__ void decide_block_rows(const GraphView<I>& g, uint32_t* T, const uint32_t* M,
                                                   const int32_t* wl_in, int n_in, int32_t* wl_out,
                                                   int32_t* cnt_out, int64_t* dsum, const PrioCfg& p,
@@ -420,9 +435,10 @@ __device__ __forceinline__ void decide_block_rows(const GraphView<I>& g, uint32_
                                                   int64_t blk_stride, uint32_t* sh) {
   for (int64_t i = blk_begin; i < n_in; i += blk_stride) {
     const int32_t v = ld<false>(wl_in + i);
+    const uint32_t t = ld<false>(T + v);
+    if (GUARD && (t == kIn || t == kOut)) continue;  // the same value in every thread
     int64_t s, e;
     row_range(g, v, s, e);
-    const uint32_t t = ld<false>(T + v);
     bool any_out = false, all_eq = true;
     if (threadIdx.x == 0) {
       const uint32_t mv = ld<NC>(M + v);
@@ -445,7 +461,8 @@ __device__ __forceinline__ void decide_block_rows(const GraphView<I>& g, uint32_
         nt = kIn;
       } else {
         nt = make_tuple(p, next_iter, (uint32_t)v);
-        wl_out[atomicAdd(cnt_out, 1)] = v;
+        const int32_t pos = atomicAdd(cnt_out, 1);
+        if (wl_out != nullptr) wl_out[pos] = v;
       }
       T[v] = nt;
       if (dsum != nullptr) atomicAdd(reinterpret_cast<unsigned long long*>(dsum), (unsigned long long)(e - s));

@@ -49,7 +49,7 @@ def test_host_only_calls(lib):
 def test_struct_sizes_match_header():
     # int64 n, nnz; int32 x2; two pointers
     assert ctypes.sizeof(mis2.mis2_csr) == 40
-    assert ctypes.sizeof(mis2.mis2_config) == 48
+    assert ctypes.sizeof(mis2.mis2_config) == 56
     assert ctypes.sizeof(mis2.mis2_stats) == 4 + 4 + 8 * 4 + 2 * 64 * 4 * 8 + 8 * 8 + 8 * 8 + 8 + 2 * (4 + 4 * 64) * 8
 
 

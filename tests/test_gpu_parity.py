@@ -246,6 +246,23 @@ def test_coarse_capacity_is_checked(loop):
     assert_level_equal(g, gpu_level(ctx, g, 0), seed=0)
 
 
+@pytest.mark.parametrize("loop", LOOPS)
+def test_no_worklist_ablation_gives_the_same_result(loop):
+    """Visiting every vertex every round (Fig. 2's variant without worklists)
+    leaves the MIS-2, the round count, the aggregates and the coarse graph
+    unchanged; only the per-round statistics (vertices visited) differ."""
+    for g in (gg.grid3d_7pt(21, 19, 17), gg.elasticity3d(6, 5, 4), gg.rmat(11, 8, seed=4), gg.grid2d_5pt(1, 1)):
+        ctx = make_ctx(g, loop=loop, ablation=mis2.MIS2_ABLATE_NO_WORKLISTS)
+        out = gpu_level(ctx, g, 2)
+        lv = oracle.coarsen_level(g, seed=2)
+        assert np.array_equal(out["in_set"], lv.in_set) and np.array_equal(out["roots"], lv.roots)
+        assert out["rounds"] == lv.rounds and out["rounds2"] == lv.rounds2
+        assert np.array_equal(out["labels"], lv.labels)
+        assert np.array_equal(out["c_colind"], lv.c_colind)
+        if out["rounds"] > 1:
+            assert int(out["trace"][1][1]) == g.n  # every vertex visited again
+
+
 def test_invalid_arguments():
     g = gg.grid2d_5pt(10, 10)
     ctx = make_ctx(g)
