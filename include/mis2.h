@@ -238,6 +238,29 @@ int mis2_coarsen_level_host(mis2_ctx* ctx, const mis2_csr* g_host, uint64_t seed
                             int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                             int64_t* n_aggs, int64_t* c_nnz, void* stream);
 
+/* Coarse edge weights (Section III-B: the coarse system of a multilevel
+ * method): c_weights[k] = the number of fine entries (u, v) of g with
+ * labels[u] = A and labels[v] = c_colind[k], for k in coarse row A; i.e. the
+ * off-diagonal of P^T A P for the 0/1 adjacency A and the 0/1 tentative
+ * prolongator P.  labels / n_aggs as mis2_aggregate returns them,
+ * c_rowptr / c_colind / c_nnz as mis2_coarsen returns them (each row
+ * ascending); c_weights (DEVICE, c_nnz int32) is written.  Synchronises;
+ * MIS2_ERR_BAD_GRAPH if an entry has no coarse counterpart. */
+int mis2_coarse_weights(mis2_ctx* ctx, const mis2_csr* g, const int32_t* labels, int64_t n_aggs,
+                        const int32_t* c_rowptr, const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights,
+                        void* stream);
+
+/* Tentative prolongator of an aggregation (Section III-B: residuals are
+ * restricted to the coarse system, its solution interpolated back): P is
+ * n x n_aggs in CSR with one entry per row, P[v, labels[v]] = 1, or
+ * 1/sqrt(|aggregate of v|) with normalize != 0 (orthonormal columns: the
+ * smoothed-aggregation tentative prolongator for a constant near-null
+ * space; IEEE double sqrt and division).  Outputs (DEVICE): p_rowptr
+ * [n+1] = 0..n, p_colind [n] = labels, p_values [n].  Asynchronous. */
+int mis2_tentative_prolongator(mis2_ctx* ctx, const int32_t* labels, int64_t n, int64_t n_aggs,
+                               int32_t normalize, int32_t* p_rowptr, int32_t* p_colind, double* p_values,
+                               void* stream);
+
 /* ------------------------------------------------------------------------
  * Batched hierarchies: many graphs, every level of their recursive
  * coarsening (Section I: multilevel methods coarsen recursively until the

@@ -6,7 +6,9 @@ shares no code with it.
 
 The arithmetic lives in plain single-threaded C (mis2_oracle.c), which follows
 the paper's Algorithm 1 (MIS-2), Algorithm 3 (aggregation; Algorithm 2 as the
-BASIC mode) and the coarse graph of Algorithm 4's setup.  This module only
+BASIC mode), the coarse graph of Algorithm 4's setup, and the two Galerkin
+pieces that follow it in a multilevel method (Section III-B): the coarse
+edge weights and the tentative prolongator.  This module only
 compiles it with gcc, marshals numpy arrays through ctypes and chains the
 calls into one coarsening level and a recursive hierarchy (Section I: coarsen
 recursively until the graph is below a threshold).
@@ -62,6 +64,10 @@ def _load():
             lib.oracle_aggregate.restype = i32
             lib.oracle_coarsen.argtypes = [i64, P, P, P, i64, P, P, P]
             lib.oracle_coarsen.restype = i32
+            lib.oracle_coarse_weights.argtypes = [i64, P, P, P, i64, P, P, P]
+            lib.oracle_coarse_weights.restype = i32
+            lib.oracle_prolongator.argtypes = [i64, P, i64, i32, P, P]
+            lib.oracle_prolongator.restype = i32
             lib.oracle_id_bits.argtypes = [i64]
             lib.oracle_id_bits.restype = i32
             lib.oracle_pack.argtypes = [u64, i64, i32]
@@ -165,6 +171,33 @@ def coarsen(g, labels, n_aggs: int):
                             _ptr(c_colind), ctypes.byref(c_nnz))
     _check(rc, "oracle_coarsen")
     return c_rowptr, c_colind[:int(c_nnz.value)]
+
+
+def coarse_weights(g, labels, n_aggs: int, c_rowptr, c_colind):
+    """Number of fine entries behind each coarse entry (int64, aligned with
+    c_colind): the off-diagonal of P^T A P for 0/1 A and P."""
+    lib = _load()
+    n, rp, ci = _csr(g)
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    crp = np.ascontiguousarray(c_rowptr, dtype=np.int64)
+    cci = np.ascontiguousarray(c_colind, dtype=np.int32)
+    w = np.zeros(max(int(crp[-1]), 1), dtype=np.int64)
+    rc = lib.oracle_coarse_weights(n, _ptr(rp), _ptr(ci), _ptr(lab), n_aggs, _ptr(crp), _ptr(cci), _ptr(w))
+    _check(rc, "oracle_coarse_weights")
+    return w[:int(crp[-1])]
+
+
+def prolongator(labels, n_aggs: int, normalize: bool = True):
+    """Tentative prolongator, one entry per row: (p_colind int32, p_values
+    float64); the row pointer is 0, 1, ..., n."""
+    lib = _load()
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    n = lab.shape[0]
+    pc = np.zeros(max(n, 1), dtype=np.int32)
+    pv = np.zeros(max(n, 1), dtype=np.float64)
+    rc = lib.oracle_prolongator(n, _ptr(lab), n_aggs, 1 if normalize else 0, _ptr(pc), _ptr(pv))
+    _check(rc, "oracle_prolongator")
+    return pc[:n], pv[:n]
 
 
 class Level:

@@ -38,6 +38,7 @@
  *     phase-2 roots ascending.
  *   - coarse rows are ascending, unique, without the diagonal.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -380,5 +381,60 @@ int oracle_coarsen(int64_t n, const int64_t* rowptr, const int32_t* colind, cons
   }
   if (c_nnz) *c_nnz = total;
   free(mptr); free(members); free(fill); free(seen); free(row);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------ Galerkin pieces */
+
+/*
+ * Weights of the coarse graph (the step after coarsen in a multilevel
+ * method, Section III-B): for coarse row A and column B, the number of fine
+ * entries (u, v) with labels[u] = A and labels[v] = B, u's row listing v.
+ * These are the off-diagonal entries of P^T A P for the 0/1 adjacency A and
+ * the 0/1 tentative prolongator P.  c_rowptr / c_colind as oracle_coarsen
+ * returns them; each entry is located by a linear scan of its coarse row.
+ */
+int oracle_coarse_weights(int64_t n, const int64_t* rowptr, const int32_t* colind, const int32_t* labels,
+                          int64_t n_aggs, const int64_t* c_rowptr, const int32_t* c_colind, int64_t* c_weights) {
+  if (n < 0 || n_aggs < 0 || !c_rowptr || (n > 0 && (!rowptr || !colind || !labels))) return ORC_ERR_ARG;
+  for (int64_t k = 0; k < c_rowptr[n_aggs]; k++) c_weights[k] = 0;
+  for (int64_t u = 0; u < n; u++) {
+    const int32_t a = labels[u];
+    for (int64_t e = rowptr[u]; e < rowptr[u + 1]; e++) {
+      const int32_t b = labels[colind[e]];
+      if (b == a) continue;
+      int64_t k = c_rowptr[a];
+      while (k < c_rowptr[a + 1] && c_colind[k] != b) k++;
+      if (k == c_rowptr[a + 1]) return ORC_ERR_ARG; /* not the coarse graph of these labels */
+      c_weights[k]++;
+    }
+  }
+  return ORC_OK;
+}
+
+/*
+ * Tentative prolongator of the aggregation (Section III-B: the coarse system
+ * receives restricted residuals and its solution is interpolated back): P is
+ * n x n_aggs with one entry per row, P[v, labels[v]] = 1, or
+ * 1 / sqrt(|aggregate|) when normalize is set (orthonormal columns: the
+ * smoothed-aggregation tentative prolongator for a constant near-null space).
+ */
+int oracle_prolongator(int64_t n, const int32_t* labels, int64_t n_aggs, int normalize, int32_t* p_colind,
+                       double* p_values) {
+  if (n < 0 || n_aggs < 0 || (n > 0 && (!labels || !p_colind || !p_values))) return ORC_ERR_ARG;
+  int64_t* size = (int64_t*)calloc((size_t)(n_aggs + 1), sizeof(int64_t));
+  if (!size) return ORC_ERR_NOMEM;
+  for (int64_t v = 0; v < n; v++) {
+    if (labels[v] < 0 || labels[v] >= n_aggs) {
+      free(size);
+      return ORC_ERR_ARG;
+    }
+    size[labels[v]]++;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    p_colind[v] = labels[v];
+    p_values[v] = normalize ? 1.0 / sqrt((double)size[labels[v]]) : 1.0;
+  }
+  free(size);
   return ORC_OK;
 }

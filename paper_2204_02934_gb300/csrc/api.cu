@@ -541,6 +541,34 @@ int mis2_coarsen_level_host(mis2_ctx* c, const mis2_csr* gh, uint64_t seed, uint
   return timer_collect(c);
 }
 
+int mis2_coarse_weights(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t n_aggs,
+                        const int32_t* c_rowptr, const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights,
+                        void* stream) {
+  if (c == nullptr || c_rowptr == nullptr) return MIS2_ERR_INVALID_ARG;
+  GraphArgs ga;
+  MIS2_TRY(validate_graph(c, g, &ga));
+  if (n_aggs < 0 || n_aggs > ga.n || (ga.n > 0 && labels == nullptr) || c_nnz < 0 ||
+      (c_nnz > 0 && (c_colind == nullptr || c_weights == nullptr)))
+    return MIS2_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
+  if (c->cfg.debug_checks & MIS2_DEBUG_VALIDATE) MIS2_TRY(check_labels(c, labels, ga.n, n_aggs, st));
+  const int rc = coarse_weights_impl(c, ga, labels, c_rowptr, c_colind, c_nnz, c_weights, st);
+  return rc == MIS2_OK ? timer_collect(c) : rc;
+}
+
+int mis2_tentative_prolongator(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int32_t normalize,
+                               int32_t* p_rowptr, int32_t* p_colind, double* p_values, void* stream) {
+  if (c == nullptr || n < 0 || n > c->max_n || n_aggs < 0 || n_aggs > n || p_rowptr == nullptr ||
+      (n > 0 && (labels == nullptr || p_colind == nullptr || p_values == nullptr)))
+    return MIS2_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  begin_call(c);
+  if (c->cfg.debug_checks & MIS2_DEBUG_VALIDATE) MIS2_TRY(check_labels(c, labels, n, n_aggs, st));
+  return prolongator_impl(c, labels, n, n_aggs, normalize, p_rowptr, p_colind, p_values, st);
+}
+
 const char* mis2_status_string(int status) {
   switch (status) {
     case MIS2_OK: return "MIS2_OK";

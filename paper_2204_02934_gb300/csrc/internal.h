@@ -222,6 +222,10 @@ bool coarsen_fast_needs_retry(const mis2_ctx* c);
 int check_graph(mis2_ctx* c, const GraphArgs& g, cudaStream_t st);
 int check_roots(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, cudaStream_t st);
 int check_labels(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, cudaStream_t st);
+int coarse_weights_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const int32_t* c_rowptr,
+                        const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights, cudaStream_t st);
+int prolongator_impl(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int normalize,
+                     int32_t* p_rowptr, int32_t* p_colind, double* p_values, cudaStream_t st);
 int coarsen_fast_finish(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                         int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, cudaStream_t st);
 int aggregate_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n_roots, uint64_t seed,

@@ -39,7 +39,7 @@ EXPORTS = [
     "mis2_batch_create", "mis2_batch_destroy", "mis2_batch_coarsen", "mis2_batch_level_sizes", "mis2_batch_labels",
     "mis2_batch_coarse", "mis2_batch_stats",
     "mis2_server_config_default", "mis2_server_create", "mis2_server_destroy", "mis2_server_submit",
-    "mis2_server_wait", "mis2_server_replay",
+    "mis2_server_wait", "mis2_server_replay", "mis2_coarse_weights", "mis2_tentative_prolongator",
 ]
 MIS2_NOALLOC_MAX_N = 262144
 
@@ -140,6 +140,8 @@ def _lib(build_if_missing: bool = False):
         "mis2_server_submit": (i32, [P, CSR, u64, pi64]),
         "mis2_server_wait": (i32, [P, i64, ctypes.POINTER(mis2_result)]),
         "mis2_server_replay": (i32, [P, i32, CSR, i64, P, P, u64, ctypes.POINTER(mis2_result), pi64]),
+        "mis2_coarse_weights": (i32, [P, CSR, P, i64, P, P, i64, P, P]),
+        "mis2_tentative_prolongator": (i32, [P, P, i64, i64, i32, P, P, P, P]),
         "mis2_status_string": (ctypes.c_char_p, [i32]),
         "mis2_last_error": (ctypes.c_char_p, []),
         "mis2_version": (ctypes.c_char_p, []),
@@ -360,6 +362,23 @@ class Context:
         na = mis2_aggregate(self.handle, dg.csr, roots, int(roots.numel()), seed, mode, labels, stream)
         return labels[:dg.n], na
 
+    def coarse_weights(self, dg: DeviceGraph, labels, n_aggs: int, c_rowptr, c_colind, stream=None):
+        import torch
+
+        w = torch.empty(max(int(c_colind.numel()), 1), dtype=torch.int32, device=dg.rowptr.device)
+        mis2_coarse_weights(self.handle, dg.csr, labels, n_aggs, c_rowptr, c_colind, w, stream)
+        return w[:int(c_colind.numel())]
+
+    def prolongator(self, labels, n_aggs: int, normalize: bool = True, stream=None):
+        import torch
+
+        n = int(labels.numel())
+        rp = torch.empty(n + 1, dtype=torch.int32, device=labels.device)
+        pc = torch.empty(max(n, 1), dtype=torch.int32, device=labels.device)
+        pv = torch.empty(max(n, 1), dtype=torch.float64, device=labels.device)
+        mis2_tentative_prolongator(self.handle, labels, n, n_aggs, normalize, rp, pc, pv, stream)
+        return rp, pc[:n], pv[:n]
+
     def coarsen(self, dg: DeviceGraph, labels, n_aggs: int, stream=None):
         import torch
 
@@ -383,6 +402,18 @@ class Context:
                                         stream)
         return dict(in_set=in_set[:dg.n], roots=roots[:nr], labels=labels[:dg.n], n_aggs=na,
                     c_rowptr=c_rowptr[:na + 1], c_colind=c_colind[:cn])
+
+
+def mis2_coarse_weights(ctx, g: mis2_csr, labels, n_aggs: int, c_rowptr, c_colind, c_weights, stream=None):
+    _check(_lib().mis2_coarse_weights(ctx, ctypes.byref(g), _ptr(labels), n_aggs, _ptr(c_rowptr), _ptr(c_colind),
+                                      int(c_colind.numel()), _ptr(c_weights), _stream(stream)), "mis2_coarse_weights")
+
+
+def mis2_tentative_prolongator(ctx, labels, n: int, n_aggs: int, normalize: bool, p_rowptr, p_colind, p_values,
+                               stream=None):
+    _check(_lib().mis2_tentative_prolongator(ctx, _ptr(labels), n, n_aggs, 1 if normalize else 0, _ptr(p_rowptr),
+                                             _ptr(p_colind), _ptr(p_values), _stream(stream)),
+           "mis2_tentative_prolongator")
 
 
 # --------------------------------------------------------------- batches

@@ -332,3 +332,46 @@ def test_table3_and_table1_full():
     t1 = tab["table1_laplace3d_100"]
     assert abs(r_fixed - t1["fixed"]) <= tab["bands"]["iters_abs"]
     assert r_star < r_fixed
+
+
+# ------------------------------------------------------------ Galerkin pieces
+def _pt_a_p(g, labels, n_aggs):
+    """P^T A P with scipy.sparse: A the 0/1 adjacency, P[v, labels[v]] = 1."""
+    sp = pytest.importorskip("scipy.sparse")
+    n = g.n
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(g.rowptr, dtype=np.int64)))
+    A = sp.csr_matrix((np.ones(len(g.colind)), (rows, np.asarray(g.colind))), shape=(n, n))
+    P = sp.csr_matrix((np.ones(n), (np.arange(n), np.asarray(labels))), shape=(n, n_aggs))
+    return (P.T @ A @ P).tocsr()
+
+
+@pytest.mark.parametrize("name,g", [("grid2d", gg.grid2d_5pt(23, 17)), ("grid3d27", gg.grid3d_27pt(9, 8, 7)),
+                                    ("rmat", gg.rmat(10, 8, seed=9)), ("gnp", gg.random_graph(300, 0.02, 5))])
+def test_coarse_weights_are_the_offdiagonal_of_galerkin_product(name, g):
+    lv = oracle.coarsen_level(g, seed=1)
+    w = oracle.coarse_weights(g, lv.labels, lv.n_aggs, lv.c_rowptr, lv.c_colind)
+    G = _pt_a_p(g, lv.labels, lv.n_aggs)
+    G.setdiag(0)
+    G.eliminate_zeros()
+    G.sort_indices()
+    assert np.array_equal(G.indptr.astype(np.int64), lv.c_rowptr)  # the coarse graph is the product's pattern
+    assert np.array_equal(G.indices, lv.c_colind)
+    assert np.array_equal(G.data.astype(np.int64), w)
+    crossing = int(np.sum(lv.labels[np.repeat(np.arange(g.n), np.diff(g.rowptr))] != lv.labels[g.colind]))
+    assert int(w.sum()) == crossing and (w >= 1).all()
+    # symmetric graph -> symmetric weights
+    assert (abs(G - G.T)).nnz == 0
+
+
+def test_prolongator_columns_and_rows():
+    g = gg.grid3d_7pt(11, 10, 9)
+    lv = oracle.coarsen_level(g, seed=4)
+    sizes = np.bincount(lv.labels, minlength=lv.n_aggs)
+    pc, pv = oracle.prolongator(lv.labels, lv.n_aggs, normalize=False)
+    assert np.array_equal(pc, lv.labels) and (pv == 1.0).all()  # piecewise constant: row sums 1
+    pc, pv = oracle.prolongator(lv.labels, lv.n_aggs, normalize=True)
+    sp = pytest.importorskip("scipy.sparse")
+    P = sp.csr_matrix((pv, (np.arange(g.n), pc)), shape=(g.n, lv.n_aggs))
+    PtP = (P.T @ P).toarray()
+    assert np.allclose(PtP, np.eye(lv.n_aggs), rtol=0, atol=4e-16 * sizes.max())  # orthonormal columns
+    assert np.array_equal(pv, 1.0 / np.sqrt(sizes[lv.labels].astype(np.float64)))
