@@ -238,6 +238,18 @@ int mis2_coarsen_level_host(mis2_ctx* ctx, const mis2_csr* g_host, uint64_t seed
                             int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                             int64_t* n_aggs, int64_t* c_nnz, void* stream);
 
+/* Distance-k maximal independent set (Section II: no two members within k
+ * hops, every vertex within k hops of one), the generalisation of
+ * Algorithm 1: each round spreads, over k hops of closed neighbourhoods,
+ * "some IN vertex within reach" and "the smallest undecided tuple within
+ * reach" (tuples of Section V); an undecided vertex becomes OUT if an IN
+ * vertex is within k hops, IN if its tuple is the smallest within k hops.
+ * k = 2 gives exactly mis2_run's set and round count, k = 1 a maximal
+ * independent set.  1 <= k <= 16.  Outputs as mis2_run; host-driven rounds
+ * over every vertex; synchronises once per round. */
+int mis2_run_k(mis2_ctx* ctx, const mis2_csr* g, int32_t k, uint64_t seed, uint8_t* in_set, int32_t* roots,
+               int64_t* n_roots, int32_t* n_rounds, void* stream);
+
 /* Coarse edge weights (Section III-B: the coarse system of a multilevel
  * method): c_weights[k] = the number of fine entries (u, v) of g with
  * labels[u] = A and labels[v] = c_colind[k], for k in coarse row A; i.e. the

@@ -64,6 +64,8 @@ def _load():
             lib.oracle_aggregate.restype = i32
             lib.oracle_coarsen.argtypes = [i64, P, P, P, i64, P, P, P]
             lib.oracle_coarsen.restype = i32
+            lib.oracle_misk.argtypes = [i64, P, P, i32, u64, i32, P, P]
+            lib.oracle_misk.restype = i32
             lib.oracle_coarse_weights.argtypes = [i64, P, P, P, i64, P, P, P]
             lib.oracle_coarse_weights.restype = i32
             lib.oracle_prolongator.argtypes = [i64, P, i64, i32, P, P]
@@ -171,6 +173,19 @@ def coarsen(g, labels, n_aggs: int):
                             _ptr(c_colind), ctypes.byref(c_nnz))
     _check(rc, "oracle_coarsen")
     return c_rowptr, c_colind[:int(c_nnz.value)]
+
+
+def misk(g, k: int, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
+    """Distance-k MIS (k = 2: Algorithm 1).  Returns (in_set uint8[n], roots
+    int32 ascending, rounds)."""
+    lib = _load()
+    n, rp, ci = _csr(g)
+    in_set = np.zeros(max(n, 1), dtype=np.uint8)
+    rounds = ctypes.c_int32(0)
+    rc = lib.oracle_misk(n, _ptr(rp), _ptr(ci), k, seed, hash_variant, _ptr(in_set), ctypes.byref(rounds))
+    _check(rc, "oracle_misk")
+    in_set = in_set[:n]
+    return in_set, np.flatnonzero(in_set).astype(np.int32), int(rounds.value)
 
 
 def coarse_weights(g, labels, n_aggs: int, c_rowptr, c_colind):

@@ -438,3 +438,93 @@ int oracle_prolongator(int64_t n, const int32_t* labels, int64_t n_aggs, int nor
   free(size);
   return ORC_OK;
 }
+
+/* ------------------------------------------------------------ MIS-k */
+
+/*
+ * Distance-k maximal independent set, the generalisation of Algorithm 1
+ * (Section II: distance-k independence; Section III-A: the column step
+ * spreads statuses one hop and decide reads one more hop, so k - 1 column
+ * steps reach distance k).  Each round, on the statuses T of the round
+ * (undecided vertices refreshed with h(iter, v) as in Algorithm 1), two
+ * quantities spread hop by hop:
+ *   B(j)_v = some IN vertex within distance j of v,
+ *   P(j)_v = the smallest undecided tuple within distance j of v (OUT when
+ *            none; IN and OUT vertices do not compete),
+ * with B(0)_v = T_v is IN, P(0)_v = T_v if undecided (else OUT), and B(j),
+ * P(j) the OR / min of B(j-1), P(j-1) over N[v].  An undecided v becomes OUT
+ * if B(k)_v, else IN if P(k)_v = T_v: the last hop is the decide step, the
+ * k - 1 before it the column steps.  All decisions of a round read the
+ * statuses from before the round.  For k = 2 this is Algorithm 1 exactly: its
+ * M_v = OUT stands for B(1)_v (the only other case, a neighbourhood decided
+ * entirely OUT, never reaches an undecided vertex's decide, since that
+ * vertex lies in the neighbourhood), and "every M_w equals T_v" is
+ * P(2)_v = T_v because each such M_w is at most T_v.  For k >= 3 the two
+ * have to stay apart: a neighbourhood decided entirely OUT blocks nothing.
+ * Every vertex is visited every round.
+ */
+int oracle_misk(int64_t n, const int64_t* rowptr, const int32_t* colind, int k, uint64_t seed, int hash_variant,
+                uint8_t* in_set, int32_t* n_rounds) {
+  if (n < 0 || k < 1 || (n > 0 && (!rowptr || !colind || !in_set))) return ORC_ERR_ARG;
+  const int b = oracle_id_bits(n);
+  uint32_t* T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+  uint32_t* Tn = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+  uint32_t* Pa = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+  uint32_t* Pb = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+  uint8_t* Ba = (uint8_t*)malloc((size_t)(n + 1));
+  uint8_t* Bb = (uint8_t*)malloc((size_t)(n + 1));
+  if (!T || !Tn || !Pa || !Pb || !Ba || !Bb) {
+    free(T); free(Tn); free(Pa); free(Pb); free(Ba); free(Bb);
+    return ORC_ERR_NOMEM;
+  }
+  for (int64_t v = 0; v < n; v++) T[v] = 1; /* any undecided value; refreshed below */
+  int64_t iter = 0, undecided = n;
+  int rc = ORC_OK;
+  while (undecided > 0) {
+    if (iter > n) { rc = ORC_ERR_NO_PROGRESS; break; }
+    for (int64_t v = 0; v < n; v++)
+      if (T[v] != ORC_IN && T[v] != ORC_OUT)
+        T[v] = oracle_pack(orc_hash(hash_variant, (uint64_t)iter, (uint64_t)v, seed), v, b);
+    /* hop 0: B(0)_v = T_v is IN, P(0)_v = T_v if undecided, else OUT */
+    for (int64_t v = 0; v < n; v++) {
+      Ba[v] = (uint8_t)(T[v] == ORC_IN);
+      Pa[v] = (T[v] == ORC_IN || T[v] == ORC_OUT) ? ORC_OUT : T[v];
+    }
+    for (int j = 1; j <= k - 1; j++) {
+      for (int64_t v = 0; v < n; v++) {
+        uint8_t bl = Ba[v];
+        uint32_t m = Pa[v];
+        for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++) {
+          bl |= Ba[colind[e]];
+          if (Pa[colind[e]] < m) m = Pa[colind[e]];
+        }
+        Bb[v] = bl;
+        Pb[v] = m;
+      }
+      uint8_t* tb = Ba; Ba = Bb; Bb = tb;
+      uint32_t* tp = Pa; Pa = Pb; Pb = tp;
+    }
+    for (int64_t v = 0; v < n; v++) {
+      Tn[v] = T[v];
+      if (T[v] == ORC_IN || T[v] == ORC_OUT) continue;
+      int blocked = Ba[v];
+      uint32_t m = Pa[v];
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++) {
+        if (Ba[colind[e]]) blocked = 1;
+        if (Pa[colind[e]] < m) m = Pa[colind[e]];
+      }
+      if (blocked) Tn[v] = ORC_OUT;
+      else if (m == T[v]) Tn[v] = ORC_IN;
+    }
+    undecided = 0;
+    for (int64_t v = 0; v < n; v++) {
+      T[v] = Tn[v];
+      undecided += (T[v] != ORC_IN && T[v] != ORC_OUT);
+    }
+    iter++;
+  }
+  for (int64_t v = 0; v < n; v++) in_set[v] = (uint8_t)(T[v] == ORC_IN);
+  if (n_rounds) *n_rounds = (int32_t)iter;
+  free(T); free(Tn); free(Pa); free(Pb); free(Ba); free(Bb);
+  return rc;
+}

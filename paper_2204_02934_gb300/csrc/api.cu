@@ -541,6 +541,19 @@ int mis2_coarsen_level_host(mis2_ctx* c, const mis2_csr* gh, uint64_t seed, uint
   return timer_collect(c);
 }
 
+int mis2_run_k(mis2_ctx* c, const mis2_csr* g, int32_t k, uint64_t seed, uint8_t* in_set, int32_t* roots,
+               int64_t* n_roots, int32_t* n_rounds, void* stream) {
+  if (c == nullptr || n_roots == nullptr || k < 1 || k > 16) return MIS2_ERR_INVALID_ARG;
+  GraphArgs ga;
+  MIS2_TRY(validate_graph(c, g, &ga));
+  if (ga.n > 0 && roots == nullptr) return MIS2_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
+  int rc = misk_impl(c, ga, k, make_prio(c, ga.n, seed), in_set, roots, n_roots, n_rounds, st);
+  return rc == MIS2_OK ? timer_collect(c) : rc;
+}
+
 int mis2_coarse_weights(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t n_aggs,
                         const int32_t* c_rowptr, const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights,
                         void* stream) {

@@ -224,6 +224,8 @@ int check_roots(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, int64_t n
 int check_labels(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, cudaStream_t st);
 int coarse_weights_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const int32_t* c_rowptr,
                         const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights, cudaStream_t st);
+int misk_impl(mis2_ctx* c, const GraphArgs& g, int k, const PrioCfg& p, uint8_t* in_set, int32_t* roots,
+              int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
 int prolongator_impl(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int normalize,
                      int32_t* p_rowptr, int32_t* p_colind, double* p_values, cudaStream_t st);
 int coarsen_fast_finish(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,

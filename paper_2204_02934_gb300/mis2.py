@@ -40,6 +40,7 @@ EXPORTS = [
     "mis2_batch_coarse", "mis2_batch_stats",
     "mis2_server_config_default", "mis2_server_create", "mis2_server_destroy", "mis2_server_submit",
     "mis2_server_wait", "mis2_server_replay", "mis2_coarse_weights", "mis2_tentative_prolongator",
+    "mis2_run_k",
 ]
 MIS2_NOALLOC_MAX_N = 262144
 
@@ -141,6 +142,7 @@ def _lib(build_if_missing: bool = False):
         "mis2_server_wait": (i32, [P, i64, ctypes.POINTER(mis2_result)]),
         "mis2_server_replay": (i32, [P, i32, CSR, i64, P, P, u64, ctypes.POINTER(mis2_result), pi64]),
         "mis2_coarse_weights": (i32, [P, CSR, P, i64, P, P, i64, P, P]),
+        "mis2_run_k": (i32, [P, CSR, i32, u64, P, P, pi64, pi32, P]),
         "mis2_tentative_prolongator": (i32, [P, P, i64, i64, i32, P, P, P, P]),
         "mis2_status_string": (ctypes.c_char_p, [i32]),
         "mis2_last_error": (ctypes.c_char_p, []),
@@ -362,6 +364,14 @@ class Context:
         na = mis2_aggregate(self.handle, dg.csr, roots, int(roots.numel()), seed, mode, labels, stream)
         return labels[:dg.n], na
 
+    def run_k(self, dg: DeviceGraph, k: int, seed: int = 0, stream=None):
+        import torch
+
+        in_set = torch.empty(max(dg.n, 1), dtype=torch.uint8, device=dg.rowptr.device)
+        roots = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.rowptr.device)
+        nr, rounds = mis2_run_k(self.handle, dg.csr, k, seed, in_set, roots, stream)
+        return in_set[:dg.n], roots[:nr], rounds
+
     def coarse_weights(self, dg: DeviceGraph, labels, n_aggs: int, c_rowptr, c_colind, stream=None):
         import torch
 
@@ -402,6 +412,14 @@ class Context:
                                         stream)
         return dict(in_set=in_set[:dg.n], roots=roots[:nr], labels=labels[:dg.n], n_aggs=na,
                     c_rowptr=c_rowptr[:na + 1], c_colind=c_colind[:cn])
+
+
+def mis2_run_k(ctx, g: mis2_csr, k: int, seed: int, in_set, roots, stream=None):
+    """Returns (n_roots, n_rounds)."""
+    nr, rounds = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(_lib().mis2_run_k(ctx, ctypes.byref(g), k, seed, _ptr(in_set), _ptr(roots), ctypes.byref(nr),
+                             ctypes.byref(rounds), _stream(stream)), "mis2_run_k")
+    return nr.value, rounds.value
 
 
 def mis2_coarse_weights(ctx, g: mis2_csr, labels, n_aggs: int, c_rowptr, c_colind, c_weights, stream=None):

@@ -375,3 +375,42 @@ def test_prolongator_columns_and_rows():
     PtP = (P.T @ P).toarray()
     assert np.allclose(PtP, np.eye(lv.n_aggs), rtol=0, atol=4e-16 * sizes.max())  # orthonormal columns
     assert np.array_equal(pv, 1.0 / np.sqrt(sizes[lv.labels].astype(np.float64)))
+
+
+# ------------------------------------------------------------ MIS-k
+def _dist_le(g, src, k):
+    """Vertices within k hops of src (BFS)."""
+    seen = {src}
+    frontier = [src]
+    for _ in range(k):
+        nxt = []
+        for u in frontier:
+            for w in g.colind[g.rowptr[u]:g.rowptr[u + 1]]:
+                if int(w) not in seen:
+                    seen.add(int(w))
+                    nxt.append(int(w))
+        frontier = nxt
+    return seen
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("seed", [0, 3])
+def test_misk_is_a_maximal_distance_k_independent_set(k, seed):
+    for g in (gg.random_graph(80, 0.05, seed + 1), gg.grid2d_5pt(9, 8), gg.rmat(7, 4, seed=seed + 2)):
+        in_set, roots, rounds = oracle.misk(g, k, seed)
+        roots = [int(r) for r in roots]
+        covered = set()
+        for r in roots:
+            ball = _dist_le(g, r, k)
+            assert not (ball - {r}) & set(roots), "two roots within distance k"
+            covered |= ball
+        assert covered == set(range(g.n)), "not maximal: a vertex is farther than k from every root"
+        assert rounds <= g.n
+
+
+def test_misk_with_k_2_is_algorithm_1():
+    for seed in range(4):
+        for g in (gg.random_graph(150, 0.03, seed), gg.grid3d_27pt(6, 5, 4), gg.rmat(9, 8, seed=seed)):
+            a = oracle.misk(g, 2, seed)
+            b = oracle.mis2(g, seed)
+            assert np.array_equal(a[0], b[0]) and a[2] == b[2]
