@@ -250,6 +250,29 @@ int mis2_coarsen_level_host(mis2_ctx* ctx, const mis2_csr* g_host, uint64_t seed
 int mis2_run_k(mis2_ctx* ctx, const mis2_csr* g, int32_t k, uint64_t seed, uint8_t* in_set, int32_t* roots,
                int64_t* n_roots, int32_t* n_rounds, void* stream);
 
+/* Colour sets for cluster multicolor Gauss-Seidel (Algorithm 4's setup:
+ * colorsets = color(A_c), meant for the coarse graph of mis2_coarsen): a
+ * distance-1 colouring, the first-fit greedy colouring in ascending order of
+ * the round-0 tuples h(0, v) (Eq. 1; seed as in mis2_run), computed by
+ * Jones-Plassmann rounds that reproduce that order exactly.  Outputs
+ * (DEVICE): colors [n]; color_ptr (capacity n + 1) and color_list [n]: the
+ * vertices of colour k, ascending, are color_list[color_ptr[k] ..
+ * color_ptr[k+1]); *n_colors and *n_rounds (host).  Self-loops are ignored.
+ * Synchronises. */
+int mis2_color(mis2_ctx* ctx, const mis2_csr* g, uint64_t seed, int32_t* colors, int32_t* color_ptr,
+               int32_t* color_list, int32_t* n_colors, int32_t* n_rounds, void* stream);
+
+/* Cluster lists of cluster multicolor Gauss-Seidel (Algorithm 4 relaxes the
+ * fine rows of one cluster in order): the fine vertices of each aggregate,
+ * ascending.  labels (DEVICE, [n]) as written by mis2_aggregate, values in
+ * [0, n_aggs); outputs (DEVICE): c_ptr [n_aggs + 1] and members [n], the
+ * vertices of aggregate a being members[c_ptr[a] .. c_ptr[a+1]).
+ * MIS2_ERR_INVALID_ARG for n > max_n, n_aggs > n, or n > 0 with n_aggs == 0;
+ * MIS2_ERR_BAD_GRAPH when a label lies outside [0, n_aggs) (the outputs are
+ * then unspecified, but nothing is written outside them).  Synchronises. */
+int mis2_cluster_lists(mis2_ctx* ctx, const int32_t* labels, int64_t n, int64_t n_aggs, int32_t* c_ptr,
+                       int32_t* members, void* stream);
+
 /* Coarse edge weights (Section III-B: the coarse system of a multilevel
  * method): c_weights[k] = the number of fine entries (u, v) of g with
  * labels[u] = A and labels[v] = c_colind[k], for k in coarse row A; i.e. the

@@ -66,6 +66,8 @@ def _load():
             lib.oracle_coarsen.restype = i32
             lib.oracle_misk.argtypes = [i64, P, P, i32, u64, i32, P, P]
             lib.oracle_misk.restype = i32
+            lib.oracle_color_greedy.argtypes = [i64, P, P, u64, i32, P, P]
+            lib.oracle_color_greedy.restype = i32
             lib.oracle_coarse_weights.argtypes = [i64, P, P, P, i64, P, P, P]
             lib.oracle_coarse_weights.restype = i32
             lib.oracle_prolongator.argtypes = [i64, P, i64, i32, P, P]
@@ -186,6 +188,40 @@ def misk(g, k: int, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
     _check(rc, "oracle_misk")
     in_set = in_set[:n]
     return in_set, np.flatnonzero(in_set).astype(np.int32), int(rounds.value)
+
+
+def color_greedy(g, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
+    """First-fit coloring in ascending round-0 tuple order: (colors int32[n],
+    n_colors)."""
+    lib = _load()
+    n, rp, ci = _csr(g)
+    colors = np.zeros(max(n, 1), dtype=np.int32)
+    nc = ctypes.c_int32(0)
+    rc = lib.oracle_color_greedy(n, _ptr(rp), _ptr(ci), seed, hash_variant, _ptr(colors), ctypes.byref(nc))
+    _check(rc, "oracle_color_greedy")
+    return colors[:n], int(nc.value)
+
+
+def group_by(keys, n_keys: int):
+    """Indices 0..n-1 grouped by key, ascending within a key: (ptr int64
+    [n_keys+1], list int32); key k owns list[ptr[k]:ptr[k+1]]."""
+    keys = np.asarray(keys)
+    ptr = np.zeros(n_keys + 1, dtype=np.int64)
+    np.add.at(ptr, keys.astype(np.int64) + 1, 1)
+    ptr = np.cumsum(ptr)
+    order = np.argsort(keys, kind="stable").astype(np.int32)
+    return ptr, order
+
+
+def color_sets(colors, n_colors: int):
+    """The colour sets of Algorithm 4 (vertices of each colour, ascending)."""
+    return group_by(colors, n_colors)
+
+
+def cluster_lists(labels, n_aggs: int):
+    """The clusters of Algorithm 4 (fine vertices of each aggregate,
+    ascending)."""
+    return group_by(labels, n_aggs)
 
 
 def coarse_weights(g, labels, n_aggs: int, c_rowptr, c_colind):

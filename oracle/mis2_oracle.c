@@ -528,3 +528,55 @@ int oracle_misk(int64_t n, const int64_t* rowptr, const int32_t* colind, int k, 
   free(T); free(Tn); free(Pa); free(Pb); free(Ba); free(Bb);
   return rc;
 }
+
+/* ------------------------------------------------------------ coloring */
+
+/*
+ * Greedy (first-fit) distance-1 coloring of a graph in ascending order of
+ * the vertices' round-0 tuples (Eq. 1 packing of h(0, v), so the order is
+ * the one a parallel Jones-Plassmann pass with those priorities
+ * reproduces): each vertex takes the smallest color no neighbour earlier in
+ * the order holds.  Used on the coarse graph for the colour sets of cluster
+ * multicolor Gauss-Seidel (Algorithm 4's setup).  Self-loops are ignored.
+ * colors int32[n]; *n_colors = 1 + the largest color (0 when n = 0).
+ */
+static const uint32_t* orc_sort_key;
+static int orc_cmp_by_key(const void* a, const void* b) {
+  const uint32_t x = orc_sort_key[*(const int64_t*)a], y = orc_sort_key[*(const int64_t*)b];
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int oracle_color_greedy(int64_t n, const int64_t* rowptr, const int32_t* colind, uint64_t seed, int hash_variant,
+                        int32_t* colors, int32_t* n_colors) {
+  if (n < 0 || (n > 0 && (!rowptr || !colind || !colors))) return ORC_ERR_ARG;
+  const int b = oracle_id_bits(n);
+  uint32_t* prio = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n + 1));
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  uint8_t* used = (uint8_t*)calloc((size_t)(n + 2), 1);
+  if (!prio || !order || !used) {
+    free(prio); free(order); free(used);
+    return ORC_ERR_NOMEM;
+  }
+  for (int64_t v = 0; v < n; v++) {
+    prio[v] = oracle_pack(orc_hash(hash_variant, 0, (uint64_t)v, seed), v, b);
+    order[v] = v;
+    colors[v] = -1;
+  }
+  orc_sort_key = prio;
+  qsort(order, (size_t)n, sizeof(int64_t), orc_cmp_by_key);
+  int32_t nc = 0;
+  for (int64_t i = 0; i < n; i++) {
+    const int64_t v = order[i];
+    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++)
+      if (colind[e] != v && colors[colind[e]] >= 0) used[colors[colind[e]]] = 1;
+    int32_t c = 0;
+    while (used[c]) c++;
+    colors[v] = c;
+    if (c + 1 > nc) nc = c + 1;
+    for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++)
+      if (colind[e] != v && colors[colind[e]] >= 0) used[colors[colind[e]]] = 0;
+  }
+  if (n_colors) *n_colors = nc;
+  free(prio); free(order); free(used);
+  return ORC_OK;
+}

@@ -166,6 +166,7 @@ static int alloc_scratch(mis2_ctx* c) {
   MIS2_TRY(dev_alloc(c, &s.large, n));
   MIS2_TRY(dev_alloc(c, &s.tmp, nnz + 4));
   MIS2_TRY(dev_alloc(c, &s.labels_tmp, n));
+  MIS2_TRY(dev_alloc(c, &s.radix, group_scratch_words(n)));
   MIS2_TRY(dev_alloc(c, &s.bitmaps, (int64_t)coarse_bitmap_blocks(c) * ((n + 31) / 32)));
   MIS2_TRY(dev_alloc(c, &s.chunk_off, n + 1));
   const int64_t giant_cap = nnz / kGiantRow + 1;
@@ -554,6 +555,19 @@ int mis2_run_k(mis2_ctx* c, const mis2_csr* g, int32_t k, uint64_t seed, uint8_t
   return rc == MIS2_OK ? timer_collect(c) : rc;
 }
 
+int mis2_color(mis2_ctx* c, const mis2_csr* g, uint64_t seed, int32_t* colors, int32_t* color_ptr,
+               int32_t* color_list, int32_t* n_colors, int32_t* n_rounds, void* stream) {
+  if (c == nullptr || n_colors == nullptr || color_ptr == nullptr) return MIS2_ERR_INVALID_ARG;
+  GraphArgs ga;
+  MIS2_TRY(validate_graph(c, g, &ga));
+  if (ga.n > 0 && (colors == nullptr || color_list == nullptr)) return MIS2_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  begin_call(c);
+  MIS2_TRY(debug_graph(c, ga, st));
+  const int rc = color_impl(c, ga, make_prio(c, ga.n, seed), colors, color_ptr, color_list, n_colors, n_rounds, st);
+  return rc == MIS2_OK ? timer_collect(c) : rc;
+}
+
 int mis2_coarse_weights(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t n_aggs,
                         const int32_t* c_rowptr, const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights,
                         void* stream) {
@@ -580,6 +594,20 @@ int mis2_tentative_prolongator(mis2_ctx* c, const int32_t* labels, int64_t n, in
   begin_call(c);
   if (c->cfg.debug_checks & MIS2_DEBUG_VALIDATE) MIS2_TRY(check_labels(c, labels, n, n_aggs, st));
   return prolongator_impl(c, labels, n, n_aggs, normalize, p_rowptr, p_colind, p_values, st);
+}
+
+int mis2_cluster_lists(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int32_t* c_ptr,
+                       int32_t* members, void* stream) {
+  if (c == nullptr || n < 0 || n > c->max_n || n_aggs < 0 || n_aggs > n || (n > 0 && n_aggs == 0) ||
+      c_ptr == nullptr || (n > 0 && (labels == nullptr || members == nullptr)))
+    return MIS2_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  begin_call(c);
+  MIS2_TRY(group_by_key(c, labels, n, n_aggs, c_ptr, members, st));
+  MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, c->s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MIS2_CUDA(cudaStreamSynchronize(st));
+  if (c->h_ctr[kCtrErr] & kErrBadGraph) return MIS2_ERR_BAD_GRAPH;
+  return timer_collect(c);
 }
 
 const char* mis2_status_string(int status) {

@@ -99,6 +99,7 @@ struct Scratch {
   int32_t* giant_slot = nullptr;  //   their bitmap slot,
   int64_t* giant_off = nullptr;   //   and their piece offsets (capacity nnz / kGiantRow + 1)
   int32_t* labels_tmp = nullptr; // labels when the caller passes none
+  int32_t* radix = nullptr;       // stable grouping: per-tile digit counts (group_scratch_words)
 };
 
 struct HostStage {  // device copies for the host-buffer entry point
@@ -226,6 +227,15 @@ int coarse_weights_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, 
                         const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights, cudaStream_t st);
 int misk_impl(mis2_ctx* c, const GraphArgs& g, int k, const PrioCfg& p, uint8_t* in_set, int32_t* roots,
               int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
+// Stable grouping of 0..n-1 by keys[i] in [0, n_keys): ptr[n_keys + 1],
+// list[n] (each key's indices ascending).  Keys outside the range set
+// kErrBadGraph in ctr[kCtrErr] (read by the caller).  Asynchronous; uses the
+// scratch arrays M, roots2, tent, qlist, agg_cnt, radix.
+int64_t group_scratch_words(int64_t n);
+int group_by_key(mis2_ctx* c, const int32_t* keys, int64_t n, int64_t n_keys, int32_t* ptr, int32_t* list,
+                 cudaStream_t st);
+int color_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* colors, int32_t* color_ptr,
+               int32_t* color_list, int32_t* n_colors, int32_t* n_rounds, cudaStream_t st);
 int prolongator_impl(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int normalize,
                      int32_t* p_rowptr, int32_t* p_colind, double* p_values, cudaStream_t st);
 int coarsen_fast_finish(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,

@@ -40,7 +40,7 @@ EXPORTS = [
     "mis2_batch_coarse", "mis2_batch_stats",
     "mis2_server_config_default", "mis2_server_create", "mis2_server_destroy", "mis2_server_submit",
     "mis2_server_wait", "mis2_server_replay", "mis2_coarse_weights", "mis2_tentative_prolongator",
-    "mis2_run_k",
+    "mis2_run_k", "mis2_color", "mis2_cluster_lists",
 ]
 MIS2_NOALLOC_MAX_N = 262144
 
@@ -143,6 +143,8 @@ def _lib(build_if_missing: bool = False):
         "mis2_server_replay": (i32, [P, i32, CSR, i64, P, P, u64, ctypes.POINTER(mis2_result), pi64]),
         "mis2_coarse_weights": (i32, [P, CSR, P, i64, P, P, i64, P, P]),
         "mis2_run_k": (i32, [P, CSR, i32, u64, P, P, pi64, pi32, P]),
+        "mis2_color": (i32, [P, CSR, u64, P, P, P, pi32, pi32, P]),
+        "mis2_cluster_lists": (i32, [P, P, i64, i64, P, P, P]),
         "mis2_tentative_prolongator": (i32, [P, P, i64, i64, i32, P, P, P, P]),
         "mis2_status_string": (ctypes.c_char_p, [i32]),
         "mis2_last_error": (ctypes.c_char_p, []),
@@ -372,6 +374,27 @@ class Context:
         nr, rounds = mis2_run_k(self.handle, dg.csr, k, seed, in_set, roots, stream)
         return in_set[:dg.n], roots[:nr], rounds
 
+    def color(self, dg: DeviceGraph, seed: int = 0, stream=None):
+        """Returns (colors, color_ptr, color_list, n_rounds)."""
+        import torch
+
+        dev = dg.rowptr.device
+        colors = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dev)
+        cptr = torch.empty(dg.n + 1, dtype=torch.int32, device=dev)
+        clist = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dev)
+        nc, rounds = mis2_color(self.handle, dg.csr, seed, colors, cptr, clist, stream)
+        return colors[:dg.n], cptr[:nc + 1], clist[:dg.n], rounds
+
+    def cluster_lists(self, labels, n_aggs: int, stream=None):
+        """Returns (c_ptr int32[n_aggs + 1], members int32[n])."""
+        import torch
+
+        n = int(labels.numel())
+        c_ptr = torch.empty(n_aggs + 1, dtype=torch.int32, device=labels.device)
+        members = torch.empty(max(n, 1), dtype=torch.int32, device=labels.device)
+        mis2_cluster_lists(self.handle, labels, n, n_aggs, c_ptr, members, stream)
+        return c_ptr, members[:n]
+
     def coarse_weights(self, dg: DeviceGraph, labels, n_aggs: int, c_rowptr, c_colind, stream=None):
         import torch
 
@@ -420,6 +443,19 @@ def mis2_run_k(ctx, g: mis2_csr, k: int, seed: int, in_set, roots, stream=None):
     _check(_lib().mis2_run_k(ctx, ctypes.byref(g), k, seed, _ptr(in_set), _ptr(roots), ctypes.byref(nr),
                              ctypes.byref(rounds), _stream(stream)), "mis2_run_k")
     return nr.value, rounds.value
+
+
+def mis2_color(ctx, g: mis2_csr, seed: int, colors, color_ptr, color_list, stream=None):
+    """Returns (n_colors, n_rounds)."""
+    nc, rounds = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(_lib().mis2_color(ctx, ctypes.byref(g), seed, _ptr(colors), _ptr(color_ptr), _ptr(color_list),
+                             ctypes.byref(nc), ctypes.byref(rounds), _stream(stream)), "mis2_color")
+    return nc.value, rounds.value
+
+
+def mis2_cluster_lists(ctx, labels, n: int, n_aggs: int, c_ptr, members, stream=None):
+    _check(_lib().mis2_cluster_lists(ctx, _ptr(labels), n, n_aggs, _ptr(c_ptr), _ptr(members), _stream(stream)),
+           "mis2_cluster_lists")
 
 
 def mis2_coarse_weights(ctx, g: mis2_csr, labels, n_aggs: int, c_rowptr, c_colind, c_weights, stream=None):

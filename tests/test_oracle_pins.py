@@ -414,3 +414,34 @@ def test_misk_with_k_2_is_algorithm_1():
             a = oracle.misk(g, 2, seed)
             b = oracle.mis2(g, seed)
             assert np.array_equal(a[0], b[0]) and a[2] == b[2]
+
+
+# ------------------------------------------------------------ coloring
+@pytest.mark.parametrize("seed", [0, 5])
+def test_greedy_coloring_is_proper_first_fit_in_priority_order(seed):
+    for g in (gg.random_graph(120, 0.05, seed + 1), gg.grid3d_27pt(5, 5, 4), gg.rmat(8, 8, seed=seed)):
+        colors, nc = oracle.color_greedy(g, seed)
+        prio = np.array([oracle.priority_tuple(0, v, g.n, seed) for v in range(g.n)], dtype=np.int64)
+        maxdeg = int(np.max(np.diff(g.rowptr))) if g.n else 0
+        assert nc == int(colors.max()) + 1 and nc <= maxdeg + 1
+        for v in range(g.n):
+            nb = [int(w) for w in g.colind[g.rowptr[v]:g.rowptr[v + 1]] if int(w) != v]
+            assert all(colors[w] != colors[v] for w in nb), "improper"
+            earlier = {int(colors[w]) for w in nb if prio[w] < prio[v]}
+            assert colors[v] == min(set(range(len(earlier) + 1)) - earlier), "not first fit in priority order"
+
+
+def test_color_sets_group_ascending():
+    colors = np.array([2, 0, 2, 1, 0, 2], dtype=np.int32)
+    ptr, lst = oracle.color_sets(colors, 3)
+    assert list(ptr) == [0, 2, 3, 6] and list(lst) == [1, 4, 3, 0, 2, 5]
+
+
+@pytest.mark.parametrize("n,n_keys", [(0, 0), (1, 1), (50, 7), (400, 400), (300, 1000)])
+def test_cluster_lists_are_the_brute_force_grouping(n, n_keys):
+    keys = gg.splitmix64(np.arange(n, dtype=np.uint64), 17) % np.uint64(max(n_keys, 1))
+    keys = keys.astype(np.int32)
+    ptr, lst = oracle.cluster_lists(keys, n_keys)
+    assert len(ptr) == n_keys + 1 and ptr[0] == 0 and ptr[-1] == n
+    for k in range(n_keys):
+        assert list(lst[ptr[k]:ptr[k + 1]]) == [v for v in range(n) if keys[v] == k]
