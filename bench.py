@@ -6,7 +6,7 @@ MIS-2 (Algorithm 1), aggregation (Algorithm 3) and the coarse graph.  The
 metric is edges/s = input entries per step / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 27pt|small|rmat|serve|ablation]
+                  [--workload 27pt|small|rmat|serve|ablation|setup]
 
 - value: device-resident input, CUDA events around each step, L2 flushed
   (256 MiB write) before every step, outside the timed interval.
@@ -543,6 +543,102 @@ def run_ablation(args):
     return 0
 
 
+def run_setup(args):
+    """The steps that follow the coarse graph in a multilevel method, on
+    GB300: the coarse edge weights and the tentative prolongator (Section
+    III-B), the colour sets (on the coarse graph) and cluster lists of
+    cluster multicolor Gauss-Seidel (Algorithm 4's setup), and distance-k MIS
+    for k = 1, 2, 3 (Algorithm 1 generalised; host-driven rounds over every
+    vertex).  Inputs resident; L2 flushed before each timed call; CUDA events
+    around each call (each synchronises).  Algorithmic bytes of the
+    bandwidth-bound steps: weights 4(n+1) + 8n + 8nnz + 8c_nnz (rowptr,
+    labels of u, colind and the labels it gathers, the coarse row searched
+    and its weights written); prolongator 28n + 4 (two reads of labels, the
+    size gather, rowptr/colind/value writes); cluster lists 4n (key
+    histogram) + per 8-bit radix pass 8n of key reads, 4n of value writes,
+    4n of value reads after the first pass and 4n of key writes before the
+    last."""
+    import torch
+
+    from paper_2204_02934_gb300 import _build, graphgen as gg, mis2
+
+    _build.build()
+    peak, peak_kind = _peaks()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    graphs = [("27-point 100^3 grid", gg.workload_27pt(100)),
+              ("R-MAT scale 20, 8 pairs per vertex", gg.rmat(20, 8, seed=42))]
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            out = fn()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            ev0.record()
+            out = fn()
+            ev1.record()
+            ev1.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        return float(np.median(ts)), out
+
+    rows = []
+    for gname, g in graphs:
+        dg = mis2.DeviceGraph.from_host(g)
+        ctx = mis2.Context(g.n, g.nnz, loop=mis2.MIS2_LOOP_DEVICE)
+        lv = ctx.coarsen_level(dg, 0)
+        labels, na = lv["labels"], int(lv["n_aggs"])
+        crp, cci = lv["c_rowptr"], lv["c_colind"]
+        cg = mis2.DeviceGraph(na, int(cci.numel()), crp, cci if cci.numel() else torch.zeros(4, dtype=torch.int32,
+                                                                                                device="cuda"))
+        c_nnz = int(cci.numel())
+        w = torch.empty(max(c_nnz, 1), dtype=torch.int32, device="cuda")
+        prp = torch.empty(g.n + 1, dtype=torch.int32, device="cuda")
+        pci = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        pvl = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        colors = torch.empty(max(na, 1), dtype=torch.int32, device="cuda")
+        cptr = torch.empty(na + 1, dtype=torch.int32, device="cuda")
+        clist = torch.empty(max(na, 1), dtype=torch.int32, device="cuda")
+        kptr = torch.empty(na + 1, dtype=torch.int32, device="cuda")
+        kmem = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        in_set = torch.empty(g.n, dtype=torch.uint8, device="cuda")
+        roots = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        base = {"graph": gname, "n": g.n, "nnz": g.nnz, "n_aggs": na, "c_nnz": c_nnz}
+
+        def add(step, ms, items, item_unit, bytes_=None, **extra):
+            r = dict(base, step=step, ms=round(ms, 4), throughput=items / (ms * 1e-3), throughput_unit=item_unit,
+                     **extra)
+            if bytes_ is not None:
+                gbs = bytes_ / (ms * 1e-3) / 1e9
+                r["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(gbs / peak, 3), "algorithmic_bytes": int(bytes_),
+                                 "peak_kind": peak_kind}
+            rows.append(r)
+
+        ms, _ = timed(lambda: mis2.mis2_coarse_weights(ctx.handle, dg.csr, labels, na, crp, cci, w))
+        add("coarse edge weights", ms, g.nnz, "fine entries/s", 4 * (g.n + 1) + 8 * g.n + 8 * g.nnz + 8 * c_nnz)
+        ms, _ = timed(lambda: mis2.mis2_tentative_prolongator(ctx.handle, labels, g.n, na, 1, prp, pci, pvl))
+        add("tentative prolongator", ms, g.n, "fine rows/s", 28 * g.n + 4)
+        ms, (nc, rounds) = timed(lambda: mis2.mis2_color(ctx.handle, cg.csr, 0, colors, cptr, clist))
+        add("colour sets of the coarse graph", ms, na, "coarse vertices/s", None, n_colors=nc, rounds=rounds)
+        passes = max(1, (max(1, (na - 1).bit_length()) + 7) // 8)
+        cl_bytes = 4 * g.n + sum(8 * g.n + 4 * g.n + (4 * g.n if p > 0 else 0) + (4 * g.n if p < passes - 1 else 0)
+                                 for p in range(passes))
+        ms, _ = timed(lambda: mis2.mis2_cluster_lists(ctx.handle, labels, g.n, na, kptr, kmem))
+        add("cluster lists", ms, g.n, "fine rows/s", cl_bytes, radix_passes=passes)
+        for k in (1, 2, 3):
+            ms, (nr, rounds) = timed(lambda: mis2.mis2_run_k(ctx.handle, dg.csr, k, 0, in_set, roots))
+            add(f"distance-{k} MIS", ms, g.nnz, "edges/s", None, set_size=nr, rounds=rounds)
+        ctx.close()
+    line = {"metric": "setup steps after the coarse graph on GB300 (time per call)", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "27-point 100^3 grid and R-MAT scale 20 (seed 42), level-0 aggregation, seed 0",
+                       "steps": args.steps, "l2": "flushed (256 MiB write) before each timed call"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _traffic_from_profile(kernel):
     """dram bytes per launch recorded by an ncu capture of this kernel, when
     the recorded source digest still matches the library sources."""
@@ -570,7 +666,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat", "serve", "ablation"])
+    ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat", "serve", "ablation",
+                                                                    "setup"])
     ap.add_argument("--loop", default="device", choices=["device", "host"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
@@ -584,6 +681,8 @@ def main():
         return run_serve(args)
     if args.workload == "ablation":
         return run_ablation(args)
+    if args.workload == "setup":
+        return run_setup(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

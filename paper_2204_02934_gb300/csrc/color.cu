@@ -7,113 +7,234 @@
 // the result is the first-fit greedy colouring in ascending tuple order,
 // whatever the schedule.  A neighbour coloured in the current round counts as
 // uncoloured (round stamps), which keeps every round's decisions on the state
-// before the round.  Host-driven rounds; then the vertices of each colour,
-// ascending, by a stable grouping on the colour.
+// before the round.  Each vertex remembers where its last blocker was found
+// and resumes there (entries before it are coloured or have larger tuples,
+// for good), so the blocked checks of all rounds read each row about once.
+// Rows are split by length: short ones get G lanes each, medium ones a warp
+// and long ones (hubs) a block.  Rounds
+// are launched in batches of kColorBatch with one count readback per batch
+// (rounds after the last one find nothing to do); then the vertices of each
+// colour, ascending, by a stable grouping on the colour.
+#include <algorithm>
+
 #include "internal.h"
+#include "teams.cuh"
 
 namespace mis2 {
 
 namespace {
 
 constexpr int32_t kUncolored = 0x7FFFFFFF;
+constexpr int64_t kColorHeavy = 2048;
+constexpr int kColorBatch = 8;
 
 __global__ void __launch_bounds__(kBlock) k_color_init(int64_t n, PrioCfg p, uint32_t* prio, int32_t* col,
-                                                       int32_t* when) {
+                                                       int32_t* when, int32_t* resume) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     prio[v] = make_tuple(p, 0u, (uint32_t)v);
     col[v] = -1;
     when[v] = kUncolored;
+    resume[v] = 0;
   }
 }
 
-// One Jones-Plassmann round, G lanes per vertex.  A vertex whose neighbours
-// use every colour of the first window of 64 looks at the next window.
-template <int G, typename I>
-__global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, const uint32_t* prio, int32_t* col,
-                                                        int32_t* when, int32_t round, int32_t* left,
-                                                        int32_t* max_color) {
-  constexpr int RPW = 32 / G;
-  const int lane = lane_id(), lg = lane & (G - 1), sub = lane / G;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// Does w keep v waiting this round?  (w uncoloured before the round, smaller
+// tuple; self-loops ignored.)
+__device__ __forceinline__ bool blocks_v(int32_t w, int64_t v, uint32_t pv, const uint32_t* prio,
+                                        const int32_t* when, int32_t round) {
+  return w != v && when[w] >= round && prio[w] < pv;
+}
+
+// One Jones-Plassmann round over the short rows, G lanes per uncoloured
+// vertex.  A vertex whose neighbours use every colour of the first window
+// of 64 looks at the next window.
+template <int G, bool PACK, typename I>
+__global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t light_max, const uint32_t* prio,
+                                                        int32_t* col, int32_t* when, int32_t* resume, int32_t round,
+                                                        int32_t* left, int32_t* max_color) {
+  const int lg = lane_id() & (G - 1);
   int32_t still = 0;
-  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW; base < g.n; base += nw * RPW) {
-    const int64_t v = base + sub;
-    const bool active = v < g.n && when[v] == kUncolored;
-    int64_t s = 0, e = 0;
-    uint32_t pv = 0;
-    if (active) {
-      row_range(g, v, s, e);
-      pv = prio[v];
-    }
-    // a smaller uncoloured neighbour (coloured this round counts as uncoloured)
-    bool blocked = false;
-    if (active)
-      visit_row<G>(g.colind, g.nnz, s, e, lg, g.vec, [&](int32_t w) {
-        if (w != v && when[w] >= round && prio[w] < pv) blocked = true;
-      });
-    blocked = group_any<G>(blocked);
-    const bool mine = active && !blocked;
-    int32_t c = -1;
-    // warp-uniform trip count: every lane takes part in the group reductions
-    for (int32_t wbase = 0; __any_sync(kFull, mine && c < 0); wbase += 64) {
-      uint32_t lo = 0, hi = 0;
-      if (mine && c < 0)
-        visit_row<G>(g.colind, g.nnz, s, e, lg, g.vec, [&](int32_t w) {
-          if (w != v && when[w] < round) {
-            const int32_t cw = col[w] - wbase;
-            if (cw >= 0 && cw < 32) lo |= 1u << cw;
-            else if (cw >= 32 && cw < 64) hi |= 1u << (cw - 32);
+  for_picked<G, PACK>(
+      g.n, [&](int64_t v) { return when[v] == kUncolored; },
+      [&](int64_t v) {
+        bool active = v >= 0;
+        int64_t s = 0, e = 0;
+        uint32_t pv = 0;
+        int32_t res = 0;
+        if (active) {
+          row_range(g, v, s, e);
+          active = e - s <= light_max;
+          pv = prio[v];
+          res = resume[v];
+        }
+        const int32_t len = active ? (int32_t)(e - s) : 0;
+        // a smaller uncoloured neighbour, from the resume point on; stop at
+        // the first chunk that holds one
+        bool blocked = false;
+        for (int32_t off = res;; off += G) {
+          const bool live = active && !blocked && off < len;
+          if (!__any_sync(kFull, live)) break;
+          bool h = false;
+          if (live && off + lg < len) h = blocks_v(__ldg(g.colind + s + off + lg), v, pv, prio, when, round);
+          if (group_any<G>(h) && live) {
+            blocked = true;
+            res = off;
           }
-        });
+        }
+        const bool mine = active && !blocked;
+        int32_t c = -1;
+        // warp-uniform trip count: every lane takes part in the group reductions
+        for (int32_t wbase = 0; __any_sync(kFull, mine && c < 0); wbase += 64) {
+          uint32_t lo = 0, hi = 0;
+          if (mine && c < 0)
+            for (int32_t off = lg; off < len; off += G) {
+              const int32_t w = __ldg(g.colind + s + off);
+              if (w != v && when[w] < round) {
+                const int32_t cw = col[w] - wbase;
+                if (cw >= 0 && cw < 32) lo |= 1u << cw;
+                else if (cw >= 32 && cw < 64) hi |= 1u << (cw - 32);
+              }
+            }
 #pragma unroll
-      for (int o = G / 2; o > 0; o >>= 1) {
-        lo |= __shfl_xor_sync(kFull, lo, o);
-        hi |= __shfl_xor_sync(kFull, hi, o);
-      }
-      if (mine && c < 0) {
-        if (~lo != 0u) c = wbase + __ffs(~lo) - 1;
-        else if (~hi != 0u) c = wbase + 32 + __ffs(~hi) - 1;
+          for (int o = G / 2; o > 0; o >>= 1) {
+            lo |= __shfl_xor_sync(kFull, lo, o);
+            hi |= __shfl_xor_sync(kFull, hi, o);
+          }
+          if (mine && c < 0) {
+            if (~lo != 0u) c = wbase + __ffs(~lo) - 1;
+            else if (~hi != 0u) c = wbase + 32 + __ffs(~hi) - 1;
+          }
+        }
+        if (lg == 0) {
+          if (mine) {
+            col[v] = c;
+            when[v] = round;
+            atomicMax(max_color, c);
+          } else if (active) {
+            resume[v] = res;
+            still++;
+          }
+        }
+      });
+  still = (int32_t)__reduce_add_sync(kFull, (unsigned)still);
+  if (lane_id() == 0 && still > 0) atomicAdd(left, still);
+}
+
+// The same round for the listed (medium or heavy) rows: a team of TPR
+// threads (a warp or the block) per row.
+template <int TPR, typename I>
+__global__ void __launch_bounds__(kBlock) k_color_list(GraphView<I> g, const int32_t* list, const int32_t* n_list,
+                                                       const uint32_t* prio, int32_t* col, int32_t* when,
+                                                       int32_t* resume, int32_t round, int32_t* left,
+                                                       int32_t* max_color) {
+  __shared__ uint32_t sh[33];
+  const Team<TPR> tm;
+  const int32_t nl = block_load(n_list);
+  int32_t still = 0;
+  for (int64_t j = tm.index; j < nl; j += tm.count) {  // team-uniform
+    const int32_t v = list[j];
+    if (when[v] != kUncolored) continue;  // team-uniform: only this team writes when[v]
+    int64_t s, e;
+    row_range(g, v, s, e);
+    const uint32_t pv = prio[v];
+    bool blocked = false;
+    int64_t p = s + resume[v];
+    for (; p < e; p += TPR) {
+      const int64_t k = p + tm.tid;
+      if (team_any<TPR>(k < e && blocks_v(__ldg(g.colind + k), v, pv, prio, when, round))) {
+        blocked = true;
+        break;
       }
     }
-    if (mine && lg == 0) {
+    if (blocked) {
+      if (tm.tid == 0) {
+        resume[v] = (int32_t)(p - s);
+        still++;
+      }
+      continue;
+    }
+    int32_t c = -1;
+    for (int32_t wbase = 0; c < 0; wbase += 64) {  // team-uniform
+      uint32_t lo = 0, hi = 0;
+      for (int64_t k = s + tm.tid; k < e; k += TPR) {
+        const int32_t w = __ldg(g.colind + k);
+        if (w != v && when[w] < round) {
+          const int32_t cw = col[w] - wbase;
+          if (cw >= 0 && cw < 32) lo |= 1u << cw;
+          else if (cw >= 32 && cw < 64) hi |= 1u << (cw - 32);
+        }
+      }
+      lo = team_or<TPR>(lo, sh);
+      hi = team_or<TPR>(hi, sh);
+      if (~lo != 0u) c = wbase + __ffs(~lo) - 1;
+      else if (~hi != 0u) c = wbase + 32 + __ffs(~hi) - 1;
+    }
+    if (tm.tid == 0) {
       col[v] = c;
       when[v] = round;
       atomicMax(max_color, c);
     }
-    if (active && !mine && lg == 0) still++;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) still += __shfl_xor_sync(kFull, still, o);
-  if (lane == 0 && still > 0) atomicAdd(left, still);
+  still = (int32_t)__reduce_add_sync(kFull, (unsigned)still);
+  if (lane_id() == 0 && still > 0) atomicAdd(left, still);
 }
 
 template <int G, typename I>
-int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const PrioCfg& p, int32_t* colors, cudaStream_t st,
-                   int32_t* rounds, int32_t* n_colors) {
+int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, const PrioCfg& p, int32_t* colors,
+                   cudaStream_t st, int32_t* rounds, int32_t* n_colors) {
   Scratch& s = c->s;
+  const int64_t light_max = G == 32 ? kColorHeavy : 64;
+  LenLists rl;
+  MIS2_TRY(classify_rows(c, ga, light_max, kColorHeavy, &rl, st));
   uint32_t* prio = s.M;
   int32_t* when = s.tent;
-  int32_t* left = s.ctr + kCtrRoots;
+  int32_t* resume = s.members;
+  int32_t* left = s.ctr + kCtrColorLeft;
   int32_t* maxc = s.ctr + kCtrM2;
   MIS2_CUDA(cudaMemsetAsync(maxc, 0xFF, sizeof(int32_t), st));
-  k_color_init<<<grid_for(c, gv.n, kBlock), kBlock, 0, st>>>(gv.n, p, prio, colors, when);
+  const int rb = grid_for(c, gv.n, kBlock);
+  k_color_init<<<rb, kBlock, 0, st>>>(gv.n, p, prio, colors, when, resume);
   c->launches++;
-  const int wb = grid_for(c, gv.n, kBlock / 32 * (32 / G));
-  int32_t r = 0;
-  for (;; r++) {
-    if (r > gv.n) return MIS2_ERR_NO_PROGRESS;
-    MIS2_CUDA(cudaMemsetAsync(left, 0, sizeof(int32_t), st));
-    k_color_round<G, I><<<wb, kBlock, 0, st>>>(gv, prio, colors, when, r, left, maxc);
-    c->launches++;
+  // packed walk (a warp per 32 vertices) once the graph fills the machine
+  const bool pack = gv.n > (int64_t)c->sm_count * 2048;
+  const int wb = pack ? grid_for(c, gv.n, kBlock) : grid_for(c, gv.n, kBlock / 32 * (32 / G));
+  const int mb = rl.n_medium > 0 ? grid_for(c, rl.n_medium, kBlock / 32) : 0;
+  const int hb = rl.n_heavy > 0 ? (int)std::min<int64_t>(rl.n_heavy, (int64_t)c->sm_count * 8) : 0;
+  for (int32_t r0 = 0;; r0 += kColorBatch) {
+    if (r0 > gv.n) return MIS2_ERR_NO_PROGRESS;
+    MIS2_CUDA(cudaMemsetAsync(left, 0, kColorBatch * sizeof(int32_t), st));
+    for (int b = 0; b < kColorBatch; b++) {
+      if (pack)
+        k_color_round<G, true, I><<<wb, kBlock, 0, st>>>(gv, light_max, prio, colors, when, resume, r0 + b,
+                                                          left + b, maxc);
+      else
+        k_color_round<G, false, I><<<wb, kBlock, 0, st>>>(gv, light_max, prio, colors, when, resume, r0 + b,
+                                                           left + b, maxc);
+      c->launches++;
+      if (mb > 0) {
+        k_color_list<32, I><<<mb, kBlock, 0, st>>>(gv, rl.medium, rl.n_medium_dev, prio, colors, when, resume,
+                                                    r0 + b, left + b, maxc);
+        c->launches++;
+      }
+      if (hb > 0) {
+        k_color_list<kBlock, I><<<hb, kBlock, 0, st>>>(gv, rl.heavy, rl.n_heavy_dev, prio, colors, when, resume,
+                                                        r0 + b, left + b, maxc);
+        c->launches++;
+      }
+    }
     MIS2_CUDA(cudaGetLastError());
-    MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MIS2_CUDA(cudaMemcpyAsync(c->h_ctr + kCtrM2, s.ctr + kCtrM2, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MIS2_CUDA(cudaMemcpyAsync(c->h_ctr + kCtrColorLeft, left, kColorBatch * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
     MIS2_CUDA(cudaStreamSynchronize(st));
-    if (c->h_ctr[kCtrRoots] == 0) break;
+    for (int b = 0; b < kColorBatch; b++)
+      if (c->h_ctr[kCtrColorLeft + b] == 0) {
+        *rounds = r0 + b + 1;
+        *n_colors = c->h_ctr[kCtrM2] + 1;
+        return MIS2_OK;
+      }
   }
-  *rounds = r + 1;
-  *n_colors = c->h_ctr[kCtrM2] + 1;
-  return MIS2_OK;
 }
 
 template <typename I>
@@ -127,8 +248,8 @@ int color_t(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* colors, 
   gv.vec = g.vec ? 1 : 0;
   gv.pad = 0;
   const double avg = g.n > 0 ? (double)g.nnz / (double)g.n : 0.0;
-  return avg < 40.0 ? color_rounds_t<4, I>(c, gv, p, colors, st, rounds, n_colors)
-                    : color_rounds_t<32, I>(c, gv, p, colors, st, rounds, n_colors);
+  return avg < 40.0 ? color_rounds_t<4, I>(c, gv, g, p, colors, st, rounds, n_colors)
+                    : color_rounds_t<32, I>(c, gv, g, p, colors, st, rounds, n_colors);
 }
 
 }  // namespace

@@ -23,10 +23,12 @@ static_assert(kRadix == kBlock, "one thread per digit in the cross-warp prefix")
 
 __device__ __forceinline__ int digit_of(int32_t key, int shift) { return (int)(((uint32_t)key >> shift) & 255u); }
 
-// cnt[d * n_tiles + t] = number of items of tile t whose digit is d.
+// cnt[d * n_tiles + t] = number of items of tile t whose digit is d.  With
+// n_keys > 0 (first pass) a key outside [0, n_keys) sets err.
 __global__ void __launch_bounds__(kBlock) k_radix_count(int64_t n, const int32_t* keys, int shift, int64_t n_tiles,
-                                                        int32_t* cnt) {
+                                                        int64_t n_keys, int32_t* cnt, int32_t* err) {
   __shared__ int32_t hist[kRadix];
+  bool bad = false;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
     hist[threadIdx.x] = 0;
     __syncthreads();
@@ -34,12 +36,17 @@ __global__ void __launch_bounds__(kBlock) k_radix_count(int64_t n, const int32_t
 #pragma unroll
     for (int k = 0; k < kRadixIpt; k++) {
       const int64_t i = base + (int64_t)k * kBlock + threadIdx.x;
-      if (i < n) atomicAdd(hist + digit_of(keys[i], shift), 1);
+      if (i < n) {
+        const int32_t key = keys[i];
+        bad |= n_keys > 0 && (key < 0 || key >= n_keys);
+        atomicAdd(hist + digit_of(key, shift), 1);
+      }
     }
     __syncthreads();
     cnt[(int64_t)threadIdx.x * n_tiles + t] = hist[threadIdx.x];
     __syncthreads();
   }
+  if (bad) atomicOr(err, kErrBadGraph);
 }
 
 // Stable scatter: item i of tile t with digit d goes to off[d * n_tiles + t]
@@ -94,14 +101,19 @@ __global__ void __launch_bounds__(kBlock) k_radix_scatter(int64_t n, const int32
   }
 }
 
-// hist[k] = number of items of key k; a key outside [0, n_keys) sets err.
-__global__ void __launch_bounds__(kBlock) k_key_hist(int64_t n, const int32_t* keys, int64_t n_keys, int32_t* hist,
-                                                     int32_t* err) {
+// ptr[k] = the first position of the sorted keys holding a key >= k (the
+// start of key k's run; empty runs included), for k in [0, n_keys].
+__global__ void __launch_bounds__(kBlock) k_run_starts(int64_t n, const int32_t* sorted, int64_t n_keys,
+                                                       int32_t* ptr) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int32_t k = keys[i];
-    if (k >= 0 && k < n_keys) atomicAdd(hist + k, 1);
-    else atomicOr(err, kErrBadGraph);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n_keys; k += stride) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)sorted[mid] < k) lo = mid + 1;
+      else hi = mid;
+    }
+    ptr[k] = (int32_t)lo;
   }
 }
 
@@ -114,15 +126,10 @@ int group_by_key(mis2_ctx* c, const int32_t* keys, int64_t n, int64_t n_keys, in
   Scratch& s = c->s;
   int32_t* err = s.ctr + kCtrErr;
   MIS2_CUDA(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
-  // run starts: key histogram, then its exclusive scan (ptr[n_keys] = n)
-  int32_t* hist = s.agg_cnt;  // n + 1 words; n_keys <= n
-  if (n_keys > 0) MIS2_CUDA(cudaMemsetAsync(hist, 0, n_keys * sizeof(int32_t), st));
-  if (n > 0) {
-    k_key_hist<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, keys, n_keys, hist, err);
-    c->launches++;
+  if (n == 0) {
+    MIS2_CUDA(cudaMemsetAsync(ptr, 0, (n_keys + 1) * sizeof(int32_t), st));
+    return MIS2_OK;
   }
-  MIS2_TRY(exclusive_scan_i32(c, hist, n_keys, ptr, nullptr, st));
-  if (n == 0) return MIS2_OK;
   // the sort: enough 8-bit passes for the largest key
   int bits = 0;
   while (bits < 31 && ((int64_t)1 << bits) < n_keys) bits++;
@@ -134,10 +141,9 @@ int group_by_key(mis2_ctx* c, const int32_t* keys, int64_t n, int64_t n_keys, in
   const int32_t* kin = keys;
   const int32_t* vin = nullptr;
   for (int p = 0; p < passes; p++) {
-    const bool last = p == passes - 1;
-    int32_t* kout = last ? nullptr : kbuf[p & 1];
-    int32_t* vout = last ? list : vbuf[p & 1];
-    k_radix_count<<<blocks, kBlock, 0, st>>>(n, kin, 8 * p, n_tiles, s.radix);
+    int32_t* kout = kbuf[p & 1];
+    int32_t* vout = p == passes - 1 ? list : vbuf[p & 1];
+    k_radix_count<<<blocks, kBlock, 0, st>>>(n, kin, 8 * p, n_tiles, p == 0 ? n_keys : 0, s.radix, err);
     MIS2_TRY(exclusive_scan_i32(c, s.radix, kRadix * n_tiles, s.radix, nullptr, st));
     k_radix_scatter<<<blocks, kBlock, 0, st>>>(n, kin, vin, 8 * p, n_tiles, s.radix, kout, vout);
     c->launches += 2;
@@ -145,6 +151,10 @@ int group_by_key(mis2_ctx* c, const int32_t* keys, int64_t n, int64_t n_keys, in
     kin = kout;
     vin = vout;
   }
+  // run starts from the sorted keys (no atomics on the keys of big groups)
+  k_run_starts<<<grid_for(c, n_keys + 1, kBlock), kBlock, 0, st>>>(n, kin, n_keys, ptr);
+  c->launches++;
+  MIS2_CUDA(cudaGetLastError());
   return MIS2_OK;
 }
 

@@ -36,6 +36,7 @@ enum : int {
   kCtrGiant = 34,    // giant member rows of the current bitmap batch
   kCtrCheckSums = 36,  // debug checks: two 64-bit entry-hash sums (words 36-39)
   kCtrInitSizes = 40,  // no-worklist mode of the host loop: round-0 list sizes (words 40-45)
+  kCtrColorLeft = 48,  // colouring: uncoloured count after each round of a batch (words 48-55)
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 40;
@@ -227,10 +228,23 @@ int coarse_weights_impl(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, 
                         const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights, cudaStream_t st);
 int misk_impl(mis2_ctx* c, const GraphArgs& g, int k, const PrioCfg& p, uint8_t* in_set, int32_t* roots,
               int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
+// Rows by length: light (<= light_max entries) for the G-lanes-per-row
+// kernels, medium (up to heavy_min) for a warp each, heavy (longer) for a
+// block each.  The lists are ascending; counts on the host and the device.
+// Uses the scratch arrays qflag, aggsize, left_mid, large.  Synchronises.
+struct LenLists {
+  const int32_t* medium = nullptr;
+  const int32_t* heavy = nullptr;
+  const int32_t* n_medium_dev = nullptr;
+  const int32_t* n_heavy_dev = nullptr;
+  int32_t n_medium = 0, n_heavy = 0;
+};
+int classify_rows(mis2_ctx* c, const GraphArgs& g, int64_t light_max, int64_t heavy_min, LenLists* rl,
+                  cudaStream_t st);
 // Stable grouping of 0..n-1 by keys[i] in [0, n_keys): ptr[n_keys + 1],
 // list[n] (each key's indices ascending).  Keys outside the range set
 // kErrBadGraph in ctr[kCtrErr] (read by the caller).  Asynchronous; uses the
-// scratch arrays M, roots2, tent, qlist, agg_cnt, radix.
+// scratch arrays M, roots2, tent, qlist, radix.
 int64_t group_scratch_words(int64_t n);
 int group_by_key(mis2_ctx* c, const int32_t* keys, int64_t n, int64_t n_keys, int32_t* ptr, int32_t* list,
                  cudaStream_t st);

@@ -47,3 +47,20 @@ def assert_level_equal(g, gpu, seed=0, mode=0, hash_variant=0):
     assert np.array_equal(gpu["c_rowptr"].astype(np.int64), lv.c_rowptr), "coarse rowptr differs"
     assert np.array_equal(gpu["c_colind"], lv.c_colind), "coarse colind differs"
     return lv
+
+
+def hub_graph(side=100, hubs=4, stride=3):
+    """A side x side 5-point grid plus `hubs` hub vertices, hub h tied to
+    every stride-th grid vertex from h on and to the other hubs: rows of a
+    few thousand entries, next to each other, among short grid rows."""
+    from paper_2204_02934_gb300 import graphgen as gg
+
+    base = gg.grid2d_5pt(side, side)
+    rows = np.repeat(np.arange(base.n, dtype=np.int64), np.diff(base.rowptr.astype(np.int64)))
+    keep = rows < base.colind
+    pairs = [np.stack([rows[keep], base.colind[keep].astype(np.int64)], axis=1)]
+    for h in range(hubs):
+        grid_v = np.arange(h, base.n, stride, dtype=np.int64)
+        pairs.append(np.stack([np.full_like(grid_v, base.n + h), grid_v], axis=1))
+        pairs.append(np.array([[base.n + h, base.n + o] for o in range(h + 1, hubs)], dtype=np.int64).reshape(-1, 2))
+    return gg.graph_from_edges(base.n + hubs, np.concatenate(pairs))

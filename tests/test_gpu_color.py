@@ -9,7 +9,7 @@ import pytest
 import oracle
 from paper_2204_02934_gb300 import graphgen as gg
 from paper_2204_02934_gb300 import mis2
-from _gpu import make_ctx
+from _gpu import hub_graph, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -33,6 +33,8 @@ def _fine():
     yield "rmat10_i64", gg.rmat(10, 8, seed=8, rowptr_dtype=np.int64)
     yield "gnp_dense", gg.random_graph(200, 0.9, 3)  # > 64 colours: several windows
     yield "single", gg.grid2d_5pt(1, 1)
+    yield "hubs", hub_graph()  # rows above the block-per-row threshold, adjacent to each other
+    yield "dense_heavy", gg.random_graph(2600, 0.85, 4)  # every row heavy, hundreds of colours
 
 
 def _coarse(g, seed=0):
@@ -58,7 +60,7 @@ def _check(g, seed):
 @pytest.mark.parametrize("name,g", list(_fine()))
 def test_coloring_matches_the_oracle(name, g, seed):
     nc = _check(g, seed)
-    if name == "gnp_dense":
+    if name in ("gnp_dense", "dense_heavy"):
         assert nc > 64
 
 

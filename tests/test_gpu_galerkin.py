@@ -8,7 +8,7 @@ import pytest
 import oracle
 from paper_2204_02934_gb300 import graphgen as gg
 from paper_2204_02934_gb300 import mis2
-from _gpu import make_ctx
+from _gpu import hub_graph, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,10 @@ def _graphs():
     yield "rmat12", gg.rmat(12, 8, seed=5)
     yield "rgg", gg.rgg2d(3000, 10.0, 4)
     yield "single", gg.grid2d_5pt(1, 1)
+    yield "hubs", hub_graph()  # long rows split over many entry chunks
+    # runs of empty rows between short ones: entry chunks span many rows
+    yield "isolated", gg.graph_from_edges(3000, [(0, 1), (1, 2), (10, 2900), (2900, 2901)] +
+                                          [(v, v + 1) for v in range(500, 2400) if v % 50])
 
 
 @pytest.mark.parametrize("name,g", list(_graphs()))

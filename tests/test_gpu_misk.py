@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2204_02934_gb300 import graphgen as gg
 from paper_2204_02934_gb300 import mis2
-from _gpu import make_ctx
+from _gpu import hub_graph, make_ctx
 
 pytestmark = pytest.mark.gpu
 
@@ -31,6 +31,7 @@ def _graphs():
     yield "rmat10_i64", gg.rmat(10, 8, seed=8, rowptr_dtype=np.int64)
     yield "gnp", gg.random_graph(400, 0.02, 3)
     yield "single", gg.grid2d_5pt(1, 1)
+    yield "hubs", hub_graph()  # rows above the block-per-row threshold
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
