@@ -557,7 +557,11 @@ def run_setup(args):
     size gather, rowptr/colind/value writes); cluster lists 4n (key
     histogram) + per 8-bit radix pass 8n of key reads, 4n of value writes,
     4n of value reads after the first pass and 4n of key writes before the
-    last."""
+    last.  cpu_baseline of each row: the oracle's restatement of the same
+    step on the same input (single-threaded C, or numpy for the grouping),
+    timed once on the host cores (skipped with --no-cpu-baseline)."""
+    import time
+
     import torch
 
     from paper_2204_02934_gb300 import _build, graphgen as gg, mis2
@@ -605,9 +609,25 @@ def run_setup(args):
         roots = torch.empty(g.n, dtype=torch.int32, device="cuda")
         base = {"graph": gname, "n": g.n, "nnz": g.nnz, "n_aggs": na, "c_nnz": c_nnz}
 
-        def add(step, ms, items, item_unit, bytes_=None, **extra):
+        h_labels = labels.cpu().numpy()
+        h_crp, h_cci = crp.cpu().numpy(), cci.cpu().numpy()
+        h_cg = gg.CSRGraph(na, h_crp.astype(np.int32), h_cci)
+
+        def cpu_time(fn):
+            if args.no_cpu_baseline:
+                return None
+            import oracle
+
+            t0 = time.perf_counter()
+            fn(oracle)
+            return {"ms": round((time.perf_counter() - t0) * 1e3, 2), "cores": 1, "kind": "oracle",
+                    "sample": "the same call on the same input, once"}
+
+        def add(step, ms, items, item_unit, bytes_=None, cpu=None, **extra):
             r = dict(base, step=step, ms=round(ms, 4), throughput=items / (ms * 1e-3), throughput_unit=item_unit,
                      **extra)
+            if cpu is not None:
+                r["cpu_baseline"] = cpu
             if bytes_ is not None:
                 gbs = bytes_ / (ms * 1e-3) / 1e9
                 r["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
@@ -616,19 +636,25 @@ def run_setup(args):
             rows.append(r)
 
         ms, _ = timed(lambda: mis2.mis2_coarse_weights(ctx.handle, dg.csr, labels, na, crp, cci, w))
-        add("coarse edge weights", ms, g.nnz, "fine entries/s", 4 * (g.n + 1) + 8 * g.n + 8 * g.nnz + 8 * c_nnz)
+        add("coarse edge weights", ms, g.nnz, "fine entries/s", 4 * (g.n + 1) + 8 * g.n + 8 * g.nnz + 8 * c_nnz,
+            cpu_time(lambda o: o.coarse_weights(g, h_labels, na, h_crp, h_cci)) if "R-MAT" not in gname else
+            {"skipped": "the oracle scans each coarse row linearly; on the R-MAT hubs that is about 30 s"})
         ms, _ = timed(lambda: mis2.mis2_tentative_prolongator(ctx.handle, labels, g.n, na, 1, prp, pci, pvl))
-        add("tentative prolongator", ms, g.n, "fine rows/s", 28 * g.n + 4)
+        add("tentative prolongator", ms, g.n, "fine rows/s", 28 * g.n + 4,
+            cpu_time(lambda o: o.prolongator(h_labels, na)))
         ms, (nc, rounds) = timed(lambda: mis2.mis2_color(ctx.handle, cg.csr, 0, colors, cptr, clist))
-        add("colour sets of the coarse graph", ms, na, "coarse vertices/s", None, n_colors=nc, rounds=rounds)
+        add("colour sets of the coarse graph", ms, na, "coarse vertices/s", None,
+            cpu_time(lambda o: o.color_sets(*o.color_greedy(h_cg, 0))), n_colors=nc, rounds=rounds)
         passes = max(1, (max(1, (na - 1).bit_length()) + 7) // 8)
         cl_bytes = 4 * g.n + sum(8 * g.n + 4 * g.n + (4 * g.n if p > 0 else 0) + (4 * g.n if p < passes - 1 else 0)
                                  for p in range(passes))
         ms, _ = timed(lambda: mis2.mis2_cluster_lists(ctx.handle, labels, g.n, na, kptr, kmem))
-        add("cluster lists", ms, g.n, "fine rows/s", cl_bytes, radix_passes=passes)
+        add("cluster lists", ms, g.n, "fine rows/s", cl_bytes, cpu_time(lambda o: o.cluster_lists(h_labels, na)),
+            radix_passes=passes)
         for k in (1, 2, 3):
             ms, (nr, rounds) = timed(lambda: mis2.mis2_run_k(ctx.handle, dg.csr, k, 0, in_set, roots))
-            add(f"distance-{k} MIS", ms, g.nnz, "edges/s", None, set_size=nr, rounds=rounds)
+            add(f"distance-{k} MIS", ms, g.nnz, "edges/s", None, cpu_time(lambda o: o.misk(g, k, 0)), set_size=nr,
+                rounds=rounds)
         ctx.close()
     line = {"metric": "setup steps after the coarse graph on GB300 (time per call)", "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
