@@ -679,7 +679,8 @@ def _traffic_from_profile(kernel):
     try:
         from paper_2204_02934_gb300 import _build
 
-        if vals.get("source_digest") != _build.source_digest():
+        files = vals["source_files"].split() if "source_files" in vals else None
+        if vals.get("source_digest") != _build.source_digest(files):
             return None
         return float(vals["dram_bytes_per_launch"])
     except Exception:

@@ -73,12 +73,17 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     return LIB_PATH
 
 
-def source_digest() -> str:
-    """sha256 over the library sources and headers (identifies a kernel build)."""
+def source_digest(files=None) -> str:
+    """sha256 over the library sources and headers (identifies a kernel
+    build); with `files` (base names), over those only: the translation unit
+    of one kernel and the headers it includes."""
     import hashlib
 
     h = hashlib.sha256()
-    for p in sorted(d for d in _deps() if not d.endswith("_build.py")):
+    deps = sorted(d for d in _deps() if not d.endswith("_build.py"))
+    if files is not None:
+        deps = [d for d in deps if os.path.basename(d) in set(files)]
+    for p in deps:
         h.update(os.path.basename(p).encode())
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]

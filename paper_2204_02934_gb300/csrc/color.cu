@@ -27,6 +27,7 @@ namespace {
 constexpr int32_t kUncolored = 0x7FFFFFFF;
 constexpr int64_t kColorHeavy = 2048;
 constexpr int kColorBatch = 8;
+constexpr int kScanU = 4;  // entries a lane tests per step of the blocked scan
 
 __global__ void __launch_bounds__(kBlock) k_color_init(int64_t n, PrioCfg p, uint32_t* prio, int32_t* col,
                                                        int32_t* when, int32_t* resume) {
@@ -72,11 +73,20 @@ __global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t 
         // a smaller uncoloured neighbour, from the resume point on; stop at
         // the first chunk that holds one
         bool blocked = false;
-        for (int32_t off = res;; off += G) {
+        for (int32_t off = res;; off += G * kScanU) {
           const bool live = active && !blocked && off < len;
           if (!__any_sync(kFull, live)) break;
           bool h = false;
-          if (live && off + lg < len) h = blocks_v(__ldg(g.colind + s + off + lg), v, pv, prio, when, round);
+          if (live) {
+            int32_t w[kScanU];  // all loads of the step first, then the tests
+#pragma unroll
+            for (int u = 0; u < kScanU; u++) {
+              const int32_t q = off + lg + u * G;
+              w[u] = q < len ? __ldg(g.colind + s + q) : (int32_t)v;  // v itself never blocks
+            }
+#pragma unroll
+            for (int u = 0; u < kScanU; u++) h |= blocks_v(w[u], v, pv, prio, when, round);
+          }
           if (group_any<G>(h) && live) {
             blocked = true;
             res = off;
@@ -121,63 +131,92 @@ __global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t 
   if (lane_id() == 0 && still > 0) atomicAdd(left, still);
 }
 
-// The same round for the listed (medium or heavy) rows: a team of TPR
-// threads (a warp or the block) per row.
+// One listed row with a team of TPR threads (a warp or the block): the
+// blocked scan from the resume point, kScanU entries a thread per step, then
+// the first-fit windows.  Returns true (on every thread) if v still waits.
 template <int TPR, typename I>
-__global__ void __launch_bounds__(kBlock) k_color_list(GraphView<I> g, const int32_t* list, const int32_t* n_list,
-                                                       const uint32_t* prio, int32_t* col, int32_t* when,
-                                                       int32_t* resume, int32_t round, int32_t* left,
-                                                       int32_t* max_color) {
-  __shared__ uint32_t sh[33];
-  const Team<TPR> tm;
-  const int32_t nl = block_load(n_list);
-  int32_t still = 0;
-  for (int64_t j = tm.index; j < nl; j += tm.count) {  // team-uniform
-    const int32_t v = list[j];
-    if (when[v] != kUncolored) continue;  // team-uniform: only this team writes when[v]
-    int64_t s, e;
-    row_range(g, v, s, e);
-    const uint32_t pv = prio[v];
-    bool blocked = false;
-    int64_t p = s + resume[v];
-    for (; p < e; p += TPR) {
-      const int64_t k = p + tm.tid;
-      if (team_any<TPR>(k < e && blocks_v(__ldg(g.colind + k), v, pv, prio, when, round))) {
-        blocked = true;
-        break;
-      }
+__device__ __forceinline__ bool color_row_team(const GraphView<I>& g, int32_t v, int tid, const uint32_t* prio,
+                                               int32_t* col, int32_t* when, int32_t* resume, int32_t round,
+                                               int32_t* max_color, uint32_t* sh) {
+  int64_t s, e;
+  row_range(g, v, s, e);
+  const uint32_t pv = prio[v];
+  int64_t p = s + resume[v];
+  for (; p < e; p += (int64_t)TPR * kScanU) {  // team-uniform
+    int32_t w[kScanU];
+#pragma unroll
+    for (int u = 0; u < kScanU; u++) {
+      const int64_t k = p + tid + (int64_t)u * TPR;
+      w[u] = k < e ? __ldg(g.colind + k) : v;
     }
-    if (blocked) {
-      if (tm.tid == 0) {
-        resume[v] = (int32_t)(p - s);
-        still++;
-      }
-      continue;
-    }
-    int32_t c = -1;
-    for (int32_t wbase = 0; c < 0; wbase += 64) {  // team-uniform
-      uint32_t lo = 0, hi = 0;
-      for (int64_t k = s + tm.tid; k < e; k += TPR) {
-        const int32_t w = __ldg(g.colind + k);
-        if (w != v && when[w] < round) {
-          const int32_t cw = col[w] - wbase;
-          if (cw >= 0 && cw < 32) lo |= 1u << cw;
-          else if (cw >= 32 && cw < 64) hi |= 1u << (cw - 32);
-        }
-      }
-      lo = team_or<TPR>(lo, sh);
-      hi = team_or<TPR>(hi, sh);
-      if (~lo != 0u) c = wbase + __ffs(~lo) - 1;
-      else if (~hi != 0u) c = wbase + 32 + __ffs(~hi) - 1;
-    }
-    if (tm.tid == 0) {
-      col[v] = c;
-      when[v] = round;
-      atomicMax(max_color, c);
+    bool h = false;
+#pragma unroll
+    for (int u = 0; u < kScanU; u++) h |= blocks_v(w[u], v, pv, prio, when, round);
+    if (team_any<TPR>(h)) {
+      if (tid == 0) resume[v] = (int32_t)(p - s);
+      return true;
     }
   }
+  int32_t c = -1;
+  for (int32_t wbase = 0; c < 0; wbase += 64) {  // team-uniform
+    uint32_t lo = 0, hi = 0;
+    for (int64_t k = s + tid; k < e; k += TPR) {
+      const int32_t w = __ldg(g.colind + k);
+      if (w != v && when[w] < round) {
+        const int32_t cw = col[w] - wbase;
+        if (cw >= 0 && cw < 32) lo |= 1u << cw;
+        else if (cw >= 32 && cw < 64) hi |= 1u << (cw - 32);
+      }
+    }
+    lo = team_or<TPR>(lo, sh);
+    hi = team_or<TPR>(hi, sh);
+    if (~lo != 0u) c = wbase + __ffs(~lo) - 1;
+    else if (~hi != 0u) c = wbase + 32 + __ffs(~hi) - 1;
+  }
+  if (tid == 0) {
+    col[v] = c;
+    when[v] = round;
+    atomicMax(max_color, c);
+  }
+  return false;
+}
+
+// The same round for the medium rows: warp per row.
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_color_medium(GraphView<I> g, const int32_t* list, const int32_t* n_list,
+                                                         const uint32_t* prio, int32_t* col, int32_t* when,
+                                                         int32_t* resume, int32_t round, int32_t* left,
+                                                         int32_t* max_color) {
+  const int lane = lane_id();
+  const int32_t nl = block_load(n_list);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t still = 0;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nl; j += nw) {  // warp-uniform
+    const int32_t v = list[j];
+    if (when[v] != kUncolored) continue;  // warp-uniform: only this warp writes when[v]
+    if (color_row_team<32, I>(g, v, lane, prio, col, when, resume, round, max_color, nullptr) && lane == 0) still++;
+  }
   still = (int32_t)__reduce_add_sync(kFull, (unsigned)still);
-  if (lane_id() == 0 && still > 0) atomicAdd(left, still);
+  if (lane == 0 && still > 0) atomicAdd(left, still);
+}
+
+// The same round for the heavy rows: block per row.
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_color_heavy(GraphView<I> g, const int32_t* list, const int32_t* n_list,
+                                                        const uint32_t* prio, int32_t* col, int32_t* when,
+                                                        int32_t* resume, int32_t round, int32_t* left,
+                                                        int32_t* max_color) {
+  __shared__ uint32_t sh[33];
+  const int32_t nl = block_load(n_list);
+  int32_t still = 0;
+  for (int64_t j = blockIdx.x; j < nl; j += gridDim.x) {  // block-uniform
+    const int32_t v = list[j];
+    if (when[v] != kUncolored) continue;  // block-uniform: only this block writes when[v]
+    if (color_row_team<kBlock, I>(g, v, threadIdx.x, prio, col, when, resume, round, max_color, sh) &&
+        threadIdx.x == 0)
+      still++;
+  }
+  if (threadIdx.x == 0 && still > 0) atomicAdd(left, still);
 }
 
 template <int G, typename I>
@@ -213,13 +252,13 @@ int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, con
                                                            left + b, maxc);
       c->launches++;
       if (mb > 0) {
-        k_color_list<32, I><<<mb, kBlock, 0, st>>>(gv, rl.medium, rl.n_medium_dev, prio, colors, when, resume,
-                                                    r0 + b, left + b, maxc);
+        k_color_medium<I><<<mb, kBlock, 0, st>>>(gv, rl.medium, rl.n_medium_dev, prio, colors, when, resume, r0 + b,
+                                                  left + b, maxc);
         c->launches++;
       }
       if (hb > 0) {
-        k_color_list<kBlock, I><<<hb, kBlock, 0, st>>>(gv, rl.heavy, rl.n_heavy_dev, prio, colors, when, resume,
-                                                        r0 + b, left + b, maxc);
+        k_color_heavy<I><<<hb, kBlock, 0, st>>>(gv, rl.heavy, rl.n_heavy_dev, prio, colors, when, resume, r0 + b,
+                                                 left + b, maxc);
         c->launches++;
       }
     }
