@@ -492,8 +492,10 @@ def run_ablation(args):
     """Fig. 2 / Table I on GB300: MIS-2 (Algorithm 1) alone on the regenerated
     Laplace3D_100 (7-point 100^3) and Elasticity3D_60 (27-point x 3 dof
     60^3), with each optimisation switched off in turn: worklists, random
-    (xorshift*) priorities -> fixed priorities or plain xorshift.  Device
-    loop, input resident, L2 flushed before each timed run."""
+    (xorshift*) priorities -> fixed priorities or plain xorshift, and the
+    packed tuple: the plain tuple engine with packed and with unpacked
+    tuples (the packing's gain is their ratio).  Device loop, input
+    resident, L2 flushed before each timed run."""
     import torch
 
     from paper_2204_02934_gb300 import _build, graphgen as gg, mis2
@@ -503,7 +505,9 @@ def run_ablation(args):
     variants = [("all optimisations", {}),
                 ("no worklists", {"ablation": mis2.MIS2_ABLATE_NO_WORKLISTS}),
                 ("fixed priorities (no random tie-break per round)", {"hash_variant": mis2.MIS2_HASH_FIXED}),
-                ("xorshift instead of xorshift*", {"hash_variant": mis2.MIS2_HASH_XORSHIFT})]
+                ("xorshift instead of xorshift*", {"hash_variant": mis2.MIS2_HASH_XORSHIFT}),
+                ("packed tuples, plain engine", {"ablation": mis2.MIS2_ABLATE_TUPLE_ENGINE}),
+                ("unpacked 3-tuples, plain engine", {"ablation": mis2.MIS2_ABLATE_UNPACKED_TUPLES})]
     graphs = [("Laplace3D_100 (7-point 100^3)", gg.grid3d_7pt(100, 100, 100)),
               ("Elasticity3D_60 (27-point x 3 dof, 60^3)", gg.elasticity3d(60, 60, 60))]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -526,14 +530,17 @@ def run_ablation(args):
                 times.append(ev0.elapsed_time(ev1))
             if ref is None:
                 ref = in_set.clone()
-            same = bool(torch.equal(in_set, ref)) if "worklists" in vname else None
+            same = bool(torch.equal(in_set, ref)) if ("worklists" in vname or "packed tuples" in vname) else None
             rows.append({"graph": gname, "n": g.n, "nnz": g.nnz, "variant": vname, "rounds": int(rounds),
                          "mis2_size": int(roots.numel()), "ms": round(float(np.median(times)), 4),
                          "same_result_as_all": same})
             ctx.close()
     base = {r["graph"]: r["ms"] for r in rows if r["variant"] == "all optimisations"}
+    plain = {r["graph"]: r["ms"] for r in rows if r["variant"] == "packed tuples, plain engine"}
     for r in rows:
         r["slowdown_vs_all"] = round(r["ms"] / base[r["graph"]], 3)
+        if r["variant"] == "unpacked 3-tuples, plain engine":
+            r["slowdown_vs_packed_plain_engine"] = round(r["ms"] / plain[r["graph"]], 3)
     line = {"metric": "MIS-2 time per variant (Fig. 2 ablation, Table I rounds) on GB300", "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "Laplace3D_100 and Elasticity3D_60 regenerated from their definitions, seed 0",

@@ -83,7 +83,8 @@ typedef struct {
   int32_t hash_variant;   /* MIS2_HASH_*; default XORSHIFT_STAR */
   int32_t agg_mode;       /* MIS2_AGG_*; default ALG3 */
   int32_t group_lanes;    /* lanes per low-degree row: 0 = pick from average degree, else 1,2,4,8,16,32 */
-  int32_t warp_degree;    /* rows with degree >= this get a full warp (default 32) */
+  int32_t warp_degree;    /* rows with degree >= this get a full warp; 0 (default) = 32 below an
+                             average degree of 40, else 256 (capped by block_degree) */
   int32_t block_degree;   /* rows with degree >= this get a full block (default 2048) */
   int32_t block_size;     /* threads per block for row kernels (default 256) */
   int32_t loop;           /* MIS2_LOOP_*; default DEVICE */
@@ -118,6 +119,19 @@ typedef struct {
  *   priorities and the xorshift hash of Fig. 2 / Table I are hash_variant
  *   values.  Per-round statistics then count the vertices visited. */
 #define MIS2_ABLATE_NO_WORKLISTS 0x1
+/* MIS2_ABLATE_TUPLE_ENGINE: mis2_run computes Algorithm 1 through a plain
+ *   engine (host-driven rounds, worklists rebuilt by ordered compaction each
+ *   round, G lanes per row) with the packed tuple of Eq. 1: the same MIS-2.
+ * MIS2_ABLATE_UNPACKED_TUPLES: the same engine with the status tuple left
+ *   unpacked (Section V-C's packing measured against, Fig. 2): status,
+ *   priority and vertex id in separate arrays, compared field by field, the
+ *   priority being the top 32 bits of h(iter, v) (Eq. 1 keeps 32 - b), so
+ *   ties the packing breaks by id may go the other way.
+ * Both apply to mis2_run alone: mis2_run_with_priorities, mis2_aggregate,
+ * mis2_coarsen_level(_host) and mis2_batch_create refuse a configuration
+ * with either set (MIS2_ERR_INVALID_ARG). */
+#define MIS2_ABLATE_TUPLE_ENGINE 0x2
+#define MIS2_ABLATE_UNPACKED_TUPLES 0x4
 
 #define MIS2_DEBUG_VALIDATE 0x1
 #define MIS2_DEBUG_FORCE_TIMEOUT 0x100

@@ -66,6 +66,8 @@ def _load():
             lib.oracle_coarsen.restype = i32
             lib.oracle_misk.argtypes = [i64, P, P, i32, u64, i32, P, P]
             lib.oracle_misk.restype = i32
+            lib.oracle_mis2_unpacked.argtypes = [i64, P, P, u64, i32, P, P]
+            lib.oracle_mis2_unpacked.restype = i32
             lib.oracle_color_greedy.argtypes = [i64, P, P, u64, i32, P, P]
             lib.oracle_color_greedy.restype = i32
             lib.oracle_coarse_weights.argtypes = [i64, P, P, P, i64, P, P, P]
@@ -186,6 +188,19 @@ def misk(g, k: int, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
     rounds = ctypes.c_int32(0)
     rc = lib.oracle_misk(n, _ptr(rp), _ptr(ci), k, seed, hash_variant, _ptr(in_set), ctypes.byref(rounds))
     _check(rc, "oracle_misk")
+    in_set = in_set[:n]
+    return in_set, np.flatnonzero(in_set).astype(np.int32), int(rounds.value)
+
+
+def mis2_unpacked(g, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
+    """Algorithm 1 with unpacked (status, priority, id) tuples, priority =
+    the top 32 hash bits.  Returns (in_set uint8[n], roots int32, rounds)."""
+    lib = _load()
+    n, rp, ci = _csr(g)
+    in_set = np.zeros(max(n, 1), dtype=np.uint8)
+    rounds = ctypes.c_int32(0)
+    rc = lib.oracle_mis2_unpacked(n, _ptr(rp), _ptr(ci), seed, hash_variant, _ptr(in_set), ctypes.byref(rounds))
+    _check(rc, "oracle_mis2_unpacked")
     in_set = in_set[:n]
     return in_set, np.flatnonzero(in_set).astype(np.int32), int(rounds.value)
 

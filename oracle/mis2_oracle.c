@@ -228,6 +228,88 @@ int oracle_mis2(int64_t n, const int64_t* rowptr, const int32_t* colind, uint64_
                           in_set, n_rounds, trace, trace_cap, NULL, 0);
 }
 
+/*
+ * Algorithm 1 with the status tuple left unpacked (the variant Section V-C's
+ * packing is measured against, Fig. 2): T_v = (status, priority, id) with
+ * status IN < UNDECIDED < OUT, priority = the top 32 bits of h(iter, v), id =
+ * v, compared field by field.  The round structure is Algorithm 1's: row
+ * refresh of the undecided vertices, column = the smallest tuple of the
+ * closed neighbourhood with IN turned into OUT, decide = OUT if some
+ * neighbour's column tuple is OUT, else IN if every one equals T_v.  Every
+ * vertex is visited each round; a decided vertex keeps its status and a
+ * column tuple that is OUT stays OUT, so this is the worklist version's
+ * result.  Self-loops and duplicate entries are harmless.
+ */
+typedef struct {
+  int status; /* 0 IN, 1 UNDECIDED, 2 OUT */
+  uint32_t prio;
+  int64_t id;
+} orc_tuple;
+
+static int orc_tuple_lt(orc_tuple a, orc_tuple b) {
+  if (a.status != b.status) return a.status < b.status;
+  if (a.prio != b.prio) return a.prio < b.prio;
+  return a.id < b.id;
+}
+
+static int orc_tuple_eq(orc_tuple a, orc_tuple b) {
+  return a.status == b.status && a.prio == b.prio && a.id == b.id;
+}
+
+int oracle_mis2_unpacked(int64_t n, const int64_t* rowptr, const int32_t* colind, uint64_t seed, int hash_variant,
+                         uint8_t* in_set, int32_t* n_rounds) {
+  if (n < 0 || (n > 0 && (!rowptr || !colind || !in_set))) return ORC_ERR_ARG;
+  orc_tuple* T = (orc_tuple*)malloc(sizeof(orc_tuple) * (size_t)(n + 1));
+  orc_tuple* M = (orc_tuple*)malloc(sizeof(orc_tuple) * (size_t)(n + 1));
+  orc_tuple* Tn = (orc_tuple*)malloc(sizeof(orc_tuple) * (size_t)(n + 1));
+  if (!T || !M || !Tn) { free(T); free(M); free(Tn); return ORC_ERR_NOMEM; }
+  const orc_tuple out = {2, 0xFFFFFFFFu, INT64_MAX};
+  for (int64_t v = 0; v < n; v++) T[v].status = 1;
+  int64_t iter = 0, undecided = n;
+  int rc = ORC_OK;
+  while (undecided > 0) {
+    if (iter > n) { rc = ORC_ERR_NO_PROGRESS; break; }
+    /* refresh row */
+    for (int64_t v = 0; v < n; v++)
+      if (T[v].status == 1) {
+        T[v].prio = (uint32_t)(orc_hash(hash_variant, (uint64_t)iter, (uint64_t)v, seed) >> 32);
+        T[v].id = v;
+      }
+    /* refresh column */
+    for (int64_t v = 0; v < n; v++) {
+      orc_tuple m = T[v];
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++)
+        if (orc_tuple_lt(T[colind[e]], m)) m = T[colind[e]];
+      M[v] = m.status == 0 ? out : m;
+    }
+    /* decide */
+    for (int64_t v = 0; v < n; v++) {
+      Tn[v] = T[v];
+      if (T[v].status != 1) continue;
+      int any_out = M[v].status == 2, all_eq = orc_tuple_eq(M[v], T[v]);
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; e++) {
+        const orc_tuple mw = M[colind[e]];
+        if (mw.status == 2) any_out = 1;
+        if (!orc_tuple_eq(mw, T[v])) all_eq = 0;
+      }
+      if (any_out) Tn[v] = out;
+      else if (all_eq) Tn[v].status = 0;
+    }
+    undecided = 0;
+    for (int64_t v = 0; v < n; v++) {
+      T[v] = Tn[v];
+      undecided += T[v].status == 1;
+    }
+    iter++;
+  }
+  for (int64_t v = 0; v < n; v++) in_set[v] = (uint8_t)(T[v].status == 0);
+  if (n_rounds) *n_rounds = (int32_t)iter;
+  free(T);
+  free(M);
+  free(Tn);
+  return rc;
+}
+
 /* ------------------------------------------------------------ Algorithm 3 */
 
 /*

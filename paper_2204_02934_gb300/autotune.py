@@ -27,7 +27,7 @@ from . import mis2
 
 DEFAULT_GRID = {
     "group_lanes": [1, 2, 4],
-    "warp_degree": [32, 64, 128],
+    "warp_degree": [32, 64, 128, 256],
     "block_degree": [1024, 2048, 8192],
     "loop_blocks_per_sm": [2, 3, 4],
 }

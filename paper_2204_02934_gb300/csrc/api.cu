@@ -82,11 +82,14 @@ static int validate_cfg(const mis2_config* cfg) {
   if (cfg->agg_mode < 0 || cfg->agg_mode > 1) return MIS2_ERR_INVALID_ARG;
   const int gl = cfg->group_lanes;
   if (gl != 0 && gl != 1 && gl != 2 && gl != 4 && gl != 8 && gl != 16 && gl != 32) return MIS2_ERR_INVALID_ARG;
-  if (cfg->warp_degree < 1 || cfg->block_degree < cfg->warp_degree) return MIS2_ERR_INVALID_ARG;
+  if (cfg->warp_degree < 0 || cfg->block_degree < 1 || cfg->block_degree < cfg->warp_degree)
+    return MIS2_ERR_INVALID_ARG;
   if (cfg->block_size != kBlock) return MIS2_ERR_INVALID_ARG;
   if (cfg->loop != MIS2_LOOP_HOST && cfg->loop != MIS2_LOOP_DEVICE) return MIS2_ERR_INVALID_ARG;
   if (cfg->spin_limit < 1 || cfg->loop_blocks_per_sm < 0) return MIS2_ERR_INVALID_ARG;
-  if ((cfg->ablation & ~MIS2_ABLATE_NO_WORKLISTS) != 0 || cfg->reserved != 0) return MIS2_ERR_INVALID_ARG;
+  if ((cfg->ablation & ~(MIS2_ABLATE_NO_WORKLISTS | MIS2_ABLATE_TUPLE_ENGINE | MIS2_ABLATE_UNPACKED_TUPLES)) != 0 ||
+      cfg->reserved != 0)
+    return MIS2_ERR_INVALID_ARG;
   return MIS2_OK;
 }
 
@@ -207,6 +210,12 @@ static int fetch_trace(mis2_ctx* c, int phase, int32_t rounds, cudaStream_t st) 
   return MIS2_OK;
 }
 
+// The tuple-engine ablation bits apply to mis2_run alone; the other calls
+// that run MIS-2 refuse a context with them set.
+static bool tuple_ablation(const mis2_ctx* c) {
+  return (c->cfg.ablation & (MIS2_ABLATE_TUPLE_ENGINE | MIS2_ABLATE_UNPACKED_TUPLES)) != 0;
+}
+
 int run_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, uint8_t* in_set, int32_t* roots, int64_t* n_roots,
              int32_t* n_rounds, cudaStream_t st) {
   int32_t r = 0;
@@ -238,7 +247,7 @@ void mis2_config_default(mis2_config* cfg) {
   cfg->hash_variant = MIS2_HASH_XORSHIFT_STAR;
   cfg->agg_mode = MIS2_AGG_ALG3;
   cfg->group_lanes = 0;
-  cfg->warp_degree = 32;
+  cfg->warp_degree = 0;
   cfg->block_degree = 2048;
   cfg->block_size = kBlock;
   cfg->loop = MIS2_LOOP_HOST;
@@ -310,14 +319,20 @@ int mis2_run(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   begin_call(c);
   MIS2_TRY(debug_graph(c, ga, st));
-  int rc = run_impl(c, ga, make_prio(c, ga.n, seed), in_set, roots, n_roots, n_rounds, st);
+  int rc;
+  if (tuple_ablation(c))
+    rc = tuple_engine_impl(c, ga, make_prio(c, ga.n, seed), (c->cfg.ablation & MIS2_ABLATE_UNPACKED_TUPLES) != 0,
+                           in_set, roots, n_roots, n_rounds, st);
+  else
+    rc = run_impl(c, ga, make_prio(c, ga.n, seed), in_set, roots, n_roots, n_rounds, st);
   if (rc == MIS2_OK) rc = timer_collect(c);
   return rc;
 }
 
 int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
                              uint8_t* in_set, int32_t* roots, int64_t* n_roots, int32_t* n_rounds, void* stream) {
-  if (c == nullptr || n_roots == nullptr || table_rounds < 0 || (table_rounds > 0 && prio_table == nullptr))
+  if (c == nullptr || n_roots == nullptr || table_rounds < 0 || (table_rounds > 0 && prio_table == nullptr) ||
+      tuple_ablation(c))
     return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -348,7 +363,7 @@ int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* pri
 
 int mis2_aggregate(mis2_ctx* c, const mis2_csr* g, const int32_t* roots, int64_t n_roots, uint64_t seed,
                    int32_t mode, int32_t* labels, int64_t* n_aggs, void* stream) {
-  if (c == nullptr || n_aggs == nullptr || (mode != MIS2_AGG_ALG3 && mode != MIS2_AGG_BASIC))
+  if (c == nullptr || n_aggs == nullptr || (mode != MIS2_AGG_ALG3 && mode != MIS2_AGG_BASIC) || tuple_ablation(c))
     return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -470,7 +485,7 @@ static int level_impl(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
 int mis2_coarsen_level(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int32_t* roots,
                        int32_t* labels, int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                        int64_t* n_aggs, int64_t* c_nnz, void* stream) {
-  if (c == nullptr) return MIS2_ERR_INVALID_ARG;
+  if (c == nullptr || tuple_ablation(c)) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
   if (c_colind_cap < 0 || (c_rowptr != nullptr && c_colind_cap > 0 && c_colind == nullptr))
@@ -505,7 +520,7 @@ static int ensure_stage(mis2_ctx* c, int64_t n, int64_t nnz) {
 int mis2_coarsen_level_host(mis2_ctx* c, const mis2_csr* gh, uint64_t seed, uint8_t* in_set, int32_t* roots,
                             int32_t* labels, int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap,
                             int64_t* n_roots, int64_t* n_aggs, int64_t* c_nnz, void* stream) {
-  if (c == nullptr || gh == nullptr) return MIS2_ERR_INVALID_ARG;
+  if (c == nullptr || gh == nullptr || tuple_ablation(c)) return MIS2_ERR_INVALID_ARG;
   if (gh->n < 0 || gh->nnz < 0 || gh->rowptr == nullptr || (gh->nnz > 0 && gh->colind == nullptr))
     return MIS2_ERR_INVALID_ARG;
   if (gh->n > c->max_n || gh->nnz > c->max_nnz) return MIS2_ERR_OUT_OF_MEMORY;

@@ -208,7 +208,8 @@ int mis2_batch_create(mis2_batch** out, int32_t max_graphs, int64_t max_total_n,
   if (out == nullptr) return MIS2_ERR_INVALID_ARG;
   *out = nullptr;
   if (max_graphs < 1 || max_total_n < 1 || max_total_nnz < 0 || max_total_n >= ((int64_t)1 << 31) ||
-      max_total_nnz >= ((int64_t)1 << 31))
+      max_total_nnz >= ((int64_t)1 << 31) ||
+      (cfg != nullptr && (cfg->ablation & (MIS2_ABLATE_TUPLE_ENGINE | MIS2_ABLATE_UNPACKED_TUPLES)) != 0))
     return MIS2_ERR_INVALID_ARG;
   mis2_batch* b = new mis2_batch();
   b->max_graphs = max_graphs;

@@ -232,7 +232,7 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.ts = c->cfg.timing ? s.loop_ts + (int64_t)trace_phase * kLoopTsWords : nullptr;
   la.labels = labels;
   la.spin_limit = c->cfg.spin_limit;
-  la.warp_degree = c->cfg.warp_degree;
+  la.warp_degree = pick_warp_degree(c, g);
   la.block_degree = c->cfg.block_degree;
   la.max_rounds = (int32_t)std::min<int64_t>(g.n, (int64_t)1 << 30);
   la.rounds_slot = rounds_slot;

@@ -173,7 +173,11 @@ void timer_end(mis2_ctx* c, cudaStream_t st);
 void timer_reset(mis2_ctx* c);
 int timer_collect(mis2_ctx* c);
 
+// Row mapping of the MIS-2 loops: lanes per low-degree row and the degree
+// from which a row gets a warp (cfg values when set, else from the average
+// degree).
 int pick_group_lanes(const mis2_ctx* c, const GraphArgs& g);
+int pick_warp_degree(const mis2_ctx* c, const GraphArgs& g);
 int grid_for(const mis2_ctx* c, int64_t items, int items_per_block, int blocks_per_sm = 8);
 
 // MIS-2 of g (labels == null) or of {v : labels[v] == -1}; leaves T with
@@ -248,6 +252,11 @@ int classify_rows(mis2_ctx* c, const GraphArgs& g, int64_t light_max, int64_t he
 int64_t group_scratch_words(int64_t n);
 int group_by_key(mis2_ctx* c, const int32_t* keys, int64_t n, int64_t n_keys, int32_t* ptr, int32_t* list,
                  cudaStream_t st);
+// Algorithm 1 through the plain tuple engine (the packed-tuple ablation):
+// packed (Eq. 1, the same MIS-2 as mis2_run) or unpacked (status, priority,
+// id) tuples.  Fills in_set / roots like mis2_run; synchronises.
+int tuple_engine_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, bool unpacked, uint8_t* in_set,
+                      int32_t* roots, int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
 int color_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* colors, int32_t* color_ptr,
                int32_t* color_list, int32_t* n_colors, int32_t* n_rounds, cudaStream_t st);
 int prolongator_impl(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int normalize,

@@ -170,17 +170,25 @@ int grid_for(const mis2_ctx* c, int64_t items, int items_per_block, int blocks_p
   return (int)b;
 }
 
+// Row mapping from the average degree (measured on GB300 over 7-/27-point
+// grids, 2-, 3- and 5-dof elasticity, random geometric graphs and R-MAT):
+// below 40 a lane per row (32 independent rows in flight per warp) and a warp
+// from 32 entries on; above it, rows of up to 255 entries stay with small
+// lane groups (16 or 8 rows in flight per warp beat a warp per row, whose
+// one row at a time leaves the loop latency-bound: 2.3-3.1x on those
+// graphs), and only longer rows get a warp.
 int pick_group_lanes(const mis2_ctx* c, const GraphArgs& g) {
   if (c->cfg.group_lanes > 0) return c->cfg.group_lanes;
   const double avg = g.n > 0 ? (double)g.nnz / (double)g.n : 0.0;
-  // A lane per row keeps 32 independent rows in flight per warp; wider
-  // groups only pay off once rows are long (heavier rows go to the warp and
-  // block classes anyway).
   if (avg < 40) return 1;
-  if (avg < 80) return 2;
-  if (avg < 160) return 4;
-  if (avg < 320) return 8;
-  return 32;
+  if (avg < 128) return 2;
+  return 4;
+}
+
+int pick_warp_degree(const mis2_ctx* c, const GraphArgs& g) {
+  if (c->cfg.warp_degree > 0) return c->cfg.warp_degree;
+  const double avg = g.n > 0 ? (double)g.nnz / (double)g.n : 0.0;
+  return std::min(avg < 40 ? 32 : 256, (int)c->cfg.block_degree);
 }
 
 template <typename I>
@@ -277,7 +285,7 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
   timer_begin(c, kKcInit, st);
   k_mis_init<I><<<grid_for(c, g.n, kBlock), kBlock, 0, st>>>(gv, labels, p, s.T, s.M, l1, l2,
                                                               s.ctr + ctr_c1(0, 0), s.ctr + ctr_c2(0, 0),
-                                                              c->cfg.warp_degree, c->cfg.block_degree);
+                                                              pick_warp_degree(c, g), c->cfg.block_degree);
   c->launches++;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());

@@ -26,7 +26,7 @@ MIS2_AGG_ALG3, MIS2_AGG_BASIC = 0, 1
 MIS2_HASH_XORSHIFT_STAR, MIS2_HASH_XORSHIFT, MIS2_HASH_FIXED = 0, 1, 2
 MIS2_LOOP_HOST, MIS2_LOOP_DEVICE = 0, 1
 MIS2_DEBUG_VALIDATE, MIS2_DEBUG_FORCE_TIMEOUT = 0x1, 0x100
-MIS2_ABLATE_NO_WORKLISTS = 0x1
+MIS2_ABLATE_NO_WORKLISTS, MIS2_ABLATE_TUPLE_ENGINE, MIS2_ABLATE_UNPACKED_TUPLES = 0x1, 0x2, 0x4
 MIS2_TRACE_CAP = 64
 MIS2_NUM_KERNEL_CLASSES = 8
 KERNEL_CLASSES = ["init", "column", "decide", "compact", "aggregate", "coarse", "device_loop", "other"]

@@ -445,3 +445,69 @@ def test_cluster_lists_are_the_brute_force_grouping(n, n_keys):
     assert len(ptr) == n_keys + 1 and ptr[0] == 0 and ptr[-1] == n
     for k in range(n_keys):
         assert list(lst[ptr[k]:ptr[k + 1]]) == [v for v in range(n) if keys[v] == k]
+
+
+# ------------------------------------------------------------ unpacked tuples
+def _unpacked_graphs():
+    yield gg.grid2d_5pt(9, 7)
+    yield gg.grid3d_27pt(4, 4, 3)
+    for seed in range(6):
+        yield gg.random_graph(40, 0.08 + 0.02 * seed, seed)
+    yield gg.rmat(7, 6, seed=3)
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_unpacked_mis2_is_a_maximal_distance2_independent_set(seed):
+    for g in _unpacked_graphs():
+        in_set, roots, rounds = oracle.mis2_unpacked(g, seed)
+        assert rounds >= 1
+        check_distance2_mis(adjacency_sets(g), roots)
+        again = oracle.mis2_unpacked(g, seed)
+        assert np.array_equal(again[0], in_set) and again[2] == rounds  # deterministic
+
+
+def test_unpacked_equals_packed_when_truncated_priorities_are_distinct():
+    # Eq. 1 keeps the top 32-b hash bits; the unpacked tuple keeps 32.  The
+    # truncation is monotone, so when the truncated priorities of every round
+    # are pairwise distinct both orders agree and Algorithm 1 takes the same
+    # steps: the two results must coincide.
+    checked = 0
+    for seed in range(4):
+        for g in _unpacked_graphs():
+            pk = oracle.mis2(g, seed)
+            up = oracle.mis2_unpacked(g, seed)
+            b = oracle.id_bits(g.n)
+            distinct = True
+            for r in range(max(pk[2], up[2])):
+                trunc = {oracle.priority_tuple(r, v, g.n, seed) >> b for v in range(g.n)}
+                distinct &= len(trunc) == g.n
+            if not distinct:
+                continue
+            checked += 1
+            assert np.array_equal(pk[0], up[0]) and pk[2] == up[2]
+    assert checked >= 20
+
+
+def test_unpacked_tuples_break_truncated_ties_by_the_full_priority():
+    # Two adjacent vertices 0 and 1 among 2^20 - 2 isolated ones (b = 20, so
+    # Eq. 1 keeps 12 priority bits).  For a seed where both draw the same 12
+    # top bits but vertex 0 the larger 30 top bits, the packed tuple breaks
+    # the tie by id (vertex 0 joins) and the unpacked one by priority
+    # (vertex 1 joins).
+    n = (1 << 20) - 2
+    assert oracle.id_bits(n) == 20
+    for seed in range(200000):
+        t12 = [oracle.priority_tuple(0, v, n, seed) >> 20 for v in (0, 1)]
+        if t12[0] != t12[1]:
+            continue
+        t30 = [oracle.priority_tuple(0, v, 1, seed) >> 2 for v in (0, 1)]
+        if t30[0] > t30[1]:
+            break
+    else:
+        pytest.fail("no seed with a 12-bit tie")
+    g = gg.graph_from_edges(n, [(0, 1)])
+    pk = oracle.mis2(g, seed)
+    up = oracle.mis2_unpacked(g, seed)
+    assert (pk[0][0], pk[0][1]) == (1, 0)
+    assert (up[0][0], up[0][1]) == (0, 1)
+    assert pk[0][2:].all() and up[0][2:].all()  # isolated vertices join
