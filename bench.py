@@ -186,6 +186,25 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(x, ws, device=None):
+    """The largest of every rank's x (torch.distributed MAX all-reduce; the
+    backend's device: cuda for NCCL, cpu for gloo)."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank, local_seconds, ws, device=None):
+    """Whole-job throughput of ws independent replicas (the method does not
+    shard): every rank's units over the slowest rank's time."""
+    return ws * units_per_rank / max_over_ranks(local_seconds, ws, device)
+
+
 def run_ours(args):
     import torch
 
@@ -251,13 +270,7 @@ def run_ours(args):
         loop_bytes += mis2_bytes(tr, n, s_bytes) + mis2_bytes(tr2, n, s_bytes)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    t_local = ms_total / 1e3
-    t_max = t_local
-    if ws > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * g.nnz * args.steps / t_max
+    value = replica_value(g.nnz * args.steps, ms_total / 1e3, ws, dev)
 
     # ---- end to end through the host-buffer entry point
     rp_h = torch.from_numpy(np.ascontiguousarray(g.rowptr)).pin_memory()
@@ -284,7 +297,7 @@ def run_ours(args):
         e2e_times.append(time.perf_counter() - t0)
         d2h = n + 4 * nr + 4 * n + 4 * (na + 1) + 4 * cn
     h2d = rp_h.numel() * rp_h.element_size() + ci_h.numel() * 4
-    e2e_val = ws * g.nnz * len(e2e_times) / sum(e2e_times)
+    e2e_val = replica_value(g.nnz * len(e2e_times), sum(e2e_times), ws, dev)
 
     if rank != 0:
         if ws > 1:
