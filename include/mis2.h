@@ -87,7 +87,8 @@ typedef struct {
                              average degree of 40, else 256 (capped by block_degree) */
   int32_t block_degree;   /* rows with degree >= this get a full block (default 2048) */
   int32_t block_size;     /* threads per block for row kernels (default 256) */
-  int32_t loop;           /* MIS2_LOOP_*; default DEVICE */
+  int32_t loop;           /* MIS2_LOOP_*; default HOST (DEVICE: one persistent launch per MIS-2 or
+                             colouring) */
   int32_t debug_checks;   /* MIS2_DEBUG_* bits (extra passes, synchronising); default 0 */
   int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
   int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = default (2) */
@@ -108,10 +109,11 @@ typedef struct {
  *   are ascending, in range and pairwise more than two hops apart, and
  *   mis2_coarsen that every label is in [0, n_aggs).  A failed check returns
  *   MIS2_ERR_BAD_GRAPH before any kernel indexes memory with the bad value.
- * MIS2_DEBUG_FORCE_TIMEOUT: test hook for the bounded waits: the device
- *   loop's grid barriers wait for one arrival more than the grid makes, so
- *   every block gives up after spin_limit polls and the call returns
- *   MIS2_ERR_TIMEOUT; the context stays usable. */
+ * MIS2_DEBUG_FORCE_TIMEOUT: test hook for the bounded waits: the grid
+ *   barriers of the device loops (MIS-2 rounds, colouring rounds) wait for
+ *   one arrival more than the grid makes, so every block gives up after
+ *   spin_limit polls and the call returns MIS2_ERR_TIMEOUT; the context
+ *   stays usable. */
 /* ablation bits (Section VI-A, Fig. 2: the optimisations one at a time).
  * MIS2_ABLATE_NO_WORKLISTS: every round visits every vertex of the
  *   (sub)graph in both steps instead of the compacted worklists (decide skips

@@ -13,10 +13,13 @@
 // Rows are split by length: short ones get G lanes each, medium ones a warp
 // and long ones (hubs) a block.  Rounds
 // are launched in batches of kColorBatch with one count readback per batch
-// (rounds after the last one find nothing to do); then the vertices of each
-// colour, ascending, by a stable grouping on the colour.
+// (rounds after the last one find nothing to do), or, with the device loop,
+// all in one persistent cooperative launch with a bounded grid barrier per
+// round; then the vertices of each colour, ascending, by a stable grouping
+// on the colour.
 #include <algorithm>
 
+#include "grid_sync.cuh"
 #include "internal.h"
 #include "teams.cuh"
 
@@ -51,9 +54,9 @@ __device__ __forceinline__ bool blocks_v(int32_t w, int64_t v, uint32_t pv, cons
 // vertex.  A vertex whose neighbours use every colour of the first window
 // of 64 looks at the next window.
 template <int G, bool PACK, typename I>
-__global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t light_max, const uint32_t* prio,
-                                                        int32_t* col, int32_t* when, int32_t* resume, int32_t round,
-                                                        int32_t* left, int32_t* max_color) {
+__device__ __forceinline__ void color_light_pass(const GraphView<I>& g, int64_t light_max, const uint32_t* prio,
+                                                 int32_t* col, int32_t* when, int32_t* resume, int32_t round,
+                                                 int32_t* left, int32_t* max_color) {
   const int lg = lane_id() & (G - 1);
   int32_t still = 0;
   for_picked<G, PACK>(
@@ -131,6 +134,13 @@ __global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t 
   if (lane_id() == 0 && still > 0) atomicAdd(left, still);
 }
 
+template <int G, bool PACK, typename I>
+__global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t light_max, const uint32_t* prio,
+                                                        int32_t* col, int32_t* when, int32_t* resume, int32_t round,
+                                                        int32_t* left, int32_t* max_color) {
+  color_light_pass<G, PACK, I>(g, light_max, prio, col, when, resume, round, left, max_color);
+}
+
 // One listed row with a team of TPR threads (a warp or the block): the
 // blocked scan from the resume point, kScanU entries a thread per step, then
 // the first-fit windows.  Returns true (on every thread) if v still waits.
@@ -183,12 +193,11 @@ __device__ __forceinline__ bool color_row_team(const GraphView<I>& g, int32_t v,
 
 // The same round for the medium rows: warp per row.
 template <typename I>
-__global__ void __launch_bounds__(kBlock) k_color_medium(GraphView<I> g, const int32_t* list, const int32_t* n_list,
-                                                         const uint32_t* prio, int32_t* col, int32_t* when,
-                                                         int32_t* resume, int32_t round, int32_t* left,
-                                                         int32_t* max_color) {
+__device__ __forceinline__ void color_medium_pass(const GraphView<I>& g, const int32_t* list, int32_t nl,
+                                                  const uint32_t* prio, int32_t* col, int32_t* when,
+                                                  int32_t* resume, int32_t round, int32_t* left,
+                                                  int32_t* max_color) {
   const int lane = lane_id();
-  const int32_t nl = block_load(n_list);
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int32_t still = 0;
   for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < nl; j += nw) {  // warp-uniform
@@ -200,14 +209,19 @@ __global__ void __launch_bounds__(kBlock) k_color_medium(GraphView<I> g, const i
   if (lane == 0 && still > 0) atomicAdd(left, still);
 }
 
-// The same round for the heavy rows: block per row.
 template <typename I>
-__global__ void __launch_bounds__(kBlock) k_color_heavy(GraphView<I> g, const int32_t* list, const int32_t* n_list,
-                                                        const uint32_t* prio, int32_t* col, int32_t* when,
-                                                        int32_t* resume, int32_t round, int32_t* left,
-                                                        int32_t* max_color) {
-  __shared__ uint32_t sh[33];
-  const int32_t nl = block_load(n_list);
+__global__ void __launch_bounds__(kBlock) k_color_medium(GraphView<I> g, const int32_t* list, const int32_t* n_list,
+                                                         const uint32_t* prio, int32_t* col, int32_t* when,
+                                                         int32_t* resume, int32_t round, int32_t* left,
+                                                         int32_t* max_color) {
+  color_medium_pass<I>(g, list, block_load(n_list), prio, col, when, resume, round, left, max_color);
+}
+
+// The same round for the heavy rows: block per row.  `sh` holds 33 words.
+template <typename I>
+__device__ __forceinline__ void color_heavy_pass(const GraphView<I>& g, const int32_t* list, int32_t nl,
+                                                 const uint32_t* prio, int32_t* col, int32_t* when, int32_t* resume,
+                                                 int32_t round, int32_t* left, int32_t* max_color, uint32_t* sh) {
   int32_t still = 0;
   for (int64_t j = blockIdx.x; j < nl; j += gridDim.x) {  // block-uniform
     const int32_t v = list[j];
@@ -217,6 +231,52 @@ __global__ void __launch_bounds__(kBlock) k_color_heavy(GraphView<I> g, const in
       still++;
   }
   if (threadIdx.x == 0 && still > 0) atomicAdd(left, still);
+}
+
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_color_heavy(GraphView<I> g, const int32_t* list, const int32_t* n_list,
+                                                        const uint32_t* prio, int32_t* col, int32_t* when,
+                                                        int32_t* resume, int32_t round, int32_t* left,
+                                                        int32_t* max_color) {
+  __shared__ uint32_t sh[33];
+  color_heavy_pass<I>(g, list, block_load(n_list), prio, col, when, resume, round, left, max_color, sh);
+}
+
+// Every round in one persistent cooperative launch: the three passes of a
+// round, one grid barrier, then every block reads the round's count of
+// vertices still waiting and stops at zero.  Counts rotate over three slots:
+// the slot zeroed in round r was last read right after barrier r - 1.
+template <int G, bool PACK, typename I>
+__global__ void __launch_bounds__(kBlock) k_color_loop(GraphView<I> g, int64_t light_max, const uint32_t* prio,
+                                                       int32_t* col, int32_t* when, int32_t* resume,
+                                                       const int32_t* medium, const int32_t* n_medium,
+                                                       const int32_t* heavy, const int32_t* n_heavy, int32_t* ctr,
+                                                       int32_t* max_color, int64_t spin_limit, int32_t max_rounds,
+                                                       int32_t barrier_extra) {
+  __shared__ uint32_t sh[33];
+  __shared__ int32_t sh_left;
+  int32_t* left = ctr + kCtrColorLeft;
+  int32_t epoch = 0;
+  const int32_t nm = block_load(n_medium), nh = block_load(n_heavy);
+  int32_t r = 0;
+  for (;; r++) {
+    int32_t* lr = left + r % 3;
+    color_light_pass<G, PACK, I>(g, light_max, prio, col, when, resume, r, lr, max_color);
+    if (nm > 0) color_medium_pass<I>(g, medium, nm, prio, col, when, resume, r, lr, max_color);
+    if (nh > 0) color_heavy_pass<I>(g, heavy, nh, prio, col, when, resume, r, lr, max_color, sh);
+    if (!grid_barrier(ctr + kCtrBarrier, epoch, ctr + kCtrErr, spin_limit, nullptr, barrier_extra)) return;
+    if (threadIdx.x == 0) sh_left = ld_volatile_i32(lr);
+    __syncthreads();
+    const int32_t still = sh_left;
+    __syncthreads();
+    if (still == 0) break;
+    if (r >= max_rounds) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(ctr + kCtrErr, kErrNoProgress);
+      break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) left[(r + 2) % 3] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctr[kCtrRounds] = r + 1;
 }
 
 template <int G, typename I>
@@ -240,6 +300,46 @@ int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, con
   const int wb = pack ? grid_for(c, gv.n, kBlock) : grid_for(c, gv.n, kBlock / 32 * (32 / G));
   const int mb = rl.n_medium > 0 ? grid_for(c, rl.n_medium, kBlock / 32) : 0;
   const int hb = rl.n_heavy > 0 ? (int)std::min<int64_t>(rl.n_heavy, (int64_t)c->sm_count * 8) : 0;
+  if (c->cfg.loop == MIS2_LOOP_DEVICE) {
+    // every round in one cooperative launch (all blocks resident)
+    auto kern = pack ? k_color_loop<G, true, I> : k_color_loop<G, false, I>;
+    int per_sm = 0;
+    MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+    if (per_sm < 1) return MIS2_ERR_CUDA;
+    const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 4;
+    const int blocks = c->sm_count * std::min(per_sm, want);
+    MIS2_CUDA(cudaMemsetAsync(left, 0, 3 * sizeof(int32_t), st));
+    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrBarrier, 0, sizeof(int32_t), st));
+    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrErr, 0, sizeof(int32_t), st));
+    GraphView<I> g = gv;
+    int64_t lm = light_max;
+    const int32_t* med = rl.medium;
+    const int32_t* nmed = rl.n_medium_dev;
+    const int32_t* hv = rl.heavy;
+    const int32_t* nhv = rl.n_heavy_dev;
+    int32_t* ctr = s.ctr;
+    int64_t spin = c->cfg.spin_limit;
+    int32_t max_rounds = (int32_t)std::min<int64_t>(gv.n, (int64_t)1 << 30);
+    int32_t extra = (c->cfg.debug_checks & MIS2_DEBUG_FORCE_TIMEOUT) ? 1 : 0;  // test hook: the waits run out
+    void* args[] = {&g,   &lm,  &prio, &colors, &when, &resume, &med,        &nmed,
+                    &hv,  &nhv, &ctr,  &maxc,   &spin, &max_rounds, &extra};
+    if (c->coop_lock != nullptr) {
+      std::lock_guard<std::mutex> lk(*c->coop_lock);
+      MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+      MIS2_CUDA(cudaEventRecord(c->coop_done, st));
+      MIS2_CUDA(cudaEventSynchronize(c->coop_done));
+    } else {
+      MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+    }
+    c->launches++;
+    MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    MIS2_CUDA(cudaStreamSynchronize(st));
+    if (c->h_ctr[kCtrErr] & kErrTimeout) return MIS2_ERR_TIMEOUT;
+    if (c->h_ctr[kCtrErr] & kErrNoProgress) return MIS2_ERR_NO_PROGRESS;
+    *rounds = c->h_ctr[kCtrRounds];
+    *n_colors = c->h_ctr[kCtrM2] + 1;
+    return MIS2_OK;
+  }
   for (int32_t r0 = 0;; r0 += kColorBatch) {
     if (r0 > gv.n) return MIS2_ERR_NO_PROGRESS;
     MIS2_CUDA(cudaMemsetAsync(left, 0, kColorBatch * sizeof(int32_t), st));

@@ -42,8 +42,8 @@ def _coarse(g, seed=0):
     return gg.CSRGraph(lv.n_aggs, lv.c_rowptr.astype(np.int32), lv.c_colind, g.name + "_coarse")
 
 
-def _check(g, seed):
-    ctx = make_ctx(g)
+def _check(g, seed, loop=mis2.MIS2_LOOP_HOST):
+    ctx = make_ctx(g, loop=loop)
     dg = mis2.DeviceGraph.from_host(g)
     colors, cptr, clist, rounds = ctx.color(dg, seed)
     ref, nc = oracle.color_greedy(g, seed)
@@ -56,10 +56,14 @@ def _check(g, seed):
     return nc
 
 
+LOOPS = [mis2.MIS2_LOOP_HOST, mis2.MIS2_LOOP_DEVICE]
+
+
+@pytest.mark.parametrize("loop", LOOPS)
 @pytest.mark.parametrize("seed", [0, 5])
 @pytest.mark.parametrize("name,g", list(_fine()))
-def test_coloring_matches_the_oracle(name, g, seed):
-    nc = _check(g, seed)
+def test_coloring_matches_the_oracle(name, g, seed, loop):
+    nc = _check(g, seed, loop)
     if name in ("gnp_dense", "dense_heavy"):
         assert nc > 64
 
@@ -67,7 +71,22 @@ def test_coloring_matches_the_oracle(name, g, seed):
 @pytest.mark.parametrize("name,g", [("grid3d27", gg.grid3d_27pt(30, 28, 26)), ("elasticity", gg.elasticity3d(8, 7, 6)),
                                     ("rmat14", gg.rmat(14, 8, seed=2))])
 def test_coarse_graph_coloring_matches_the_oracle(name, g):
-    _check(_coarse(g, 3), 3)
+    for loop in LOOPS:
+        _check(_coarse(g, 3), 3, loop)
+
+
+def test_device_loop_timeout_reports_and_recovers():
+    g = gg.grid3d_27pt(20, 18, 16)
+    dg = mis2.DeviceGraph.from_host(g)
+    ctx = make_ctx(g, loop=mis2.MIS2_LOOP_DEVICE, debug_checks=mis2.MIS2_DEBUG_FORCE_TIMEOUT, spin_limit=2000)
+    with pytest.raises(mis2.Mis2Error) as e:
+        ctx.color(dg, 0)
+    assert e.value.status == -5  # MIS2_ERR_TIMEOUT
+    cfg = mis2.mis2_config_default()
+    cfg.loop = mis2.MIS2_LOOP_DEVICE
+    mis2.mis2_ctx_set_config(ctx.handle, cfg)
+    colors, _, _, _ = ctx.color(dg, 0)
+    assert np.array_equal(colors.cpu().numpy(), oracle.color_greedy(g, 0)[0])
 
 
 def test_empty_graph():
