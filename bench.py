@@ -139,6 +139,24 @@ def _dist():
     return ws, rank, local
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86: "model name"; Arm: the
+    implementer / part codes), else the machine type."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model name"):
+        for ln in info:
+            if ln.startswith(key) and ":" in ln:
+                return ln.split(":", 1)[1].strip()
+    impl = next((ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU implementer")), None)
+    part = next((ln.split(":", 1)[1].strip() for ln in info if ln.startswith("CPU part")), None)
+    if impl or part:
+        return f"{platform.machine()} (CPU implementer {impl}, part {part})"
+    return platform.machine()
+
+
 def _cpu_baseline(g, budget_s=12.0):
     """The oracle, as it stands, on the same graph: repeat full levels until
     about budget_s of CPU time is spent (at least one)."""
@@ -155,7 +173,7 @@ def _cpu_baseline(g, budget_s=12.0):
             break
     return {"value": g.nnz * reps / el, "unit": "edges/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} full coarsening level(s) of the same graph, single-threaded C oracle, "
-                      f"{el:.1f} s on {platform.machine()} ({os.cpu_count()} cores present)"}
+                      f"{el:.1f} s on {cpu_model()} ({os.cpu_count()} cores present)"}
 
 
 def run_reference(args):
@@ -180,7 +198,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "config": {"workload": desc, "n": g.n, "nnz": g.nnz},
             "cpu_baseline": {"value": val, "unit": "edges/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} full levels of the workload graph, single-threaded C oracle"},
+                             "sample": f"{len(times)} full levels of the workload graph, single-threaded C oracle "
+                                       f"on {cpu_model()}"},
             "e2e": {"value": val, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
