@@ -1,14 +1,16 @@
 """CPU oracle for MIS-2, MIS-2 aggregation and the coarse graph.
 
 TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
-CPU-baseline leg may import this package; the CUDA library never calls it and
-shares no code with it.
+CPU-baseline and reference legs may import this package; the CUDA library
+never calls it and shares no code with it.
 
 The arithmetic lives in plain single-threaded C (mis2_oracle.c), which follows
 the paper's Algorithm 1 (MIS-2), Algorithm 3 (aggregation; Algorithm 2 as the
 BASIC mode), the coarse graph of Algorithm 4's setup, and the two Galerkin
 pieces that follow it in a multilevel method (Section III-B): the coarse
-edge weights and the tentative prolongator.  This module only
+edge weights and the tentative prolongator; distance-k MIS, Algorithm 1 with
+unpacked tuples, and the colouring of Algorithm 4's setup (the colour sets
+and cluster lists are stable groupings written here in numpy).  This module only
 compiles it with gcc, marshals numpy arrays through ctypes and chains the
 calls into one coarsening level and a recursive hierarchy (Section I: coarsen
 recursively until the graph is below a threshold).

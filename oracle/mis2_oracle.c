@@ -4,7 +4,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the yardstick the CUDA library is
  * checked against.  Only the test suite, the smoke check and the CPU-baseline
- * leg of the benchmark may load it.  It shares no code with the CUDA path:
+ * and reference legs of the benchmark may load it.  It shares no code with the CUDA path:
  * every constant and helper below is written out here on its own.
  *
  * It follows the paper (Kelley & Rajamanickam, "Parallel, Portable
@@ -18,6 +18,21 @@
  *   oracle_coarsen    the coarse graph A_c of Algorithm 4's setup (Section
  *                     III-C): one vertex per aggregate, an edge wherever two
  *                     aggregates are joined by a fine edge.
+ *   oracle_coarse_weights, oracle_prolongator
+ *                     the off-diagonal of P^T A P and the tentative
+ *                     prolongator (Section III-B, the step after coarsening).
+ *   oracle_misk       distance-k MIS, Algorithm 1 generalised (Section II).
+ *   oracle_mis2_unpacked
+ *                     Algorithm 1 with unpacked (status, priority, id)
+ *                     tuples (what Section V-C's packing is measured against).
+ *   oracle_color_greedy
+ *                     the colouring of Algorithm 4's setup: first fit in
+ *                     ascending round-0 tuple order.
+ *
+ * Every function is pinned by tests to something other than itself (the
+ * worked example of Fig. 1, brute-force definitions, scipy's sparse
+ * products, equality with another function where the paper says they
+ * agree); none is parity-unpinned.
  *
  * Readings where the paper is silent (they bind the CUDA path too):
  *   - adj(v) in the column and decide steps is the CLOSED neighbourhood
