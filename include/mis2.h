@@ -55,7 +55,8 @@ typedef enum {
   MIS2_ERR_CUDA = -3,          /* a CUDA runtime call failed; see mis2_last_error() */
   MIS2_ERR_BAD_GRAPH = -4,     /* debug_checks: malformed CSR, or roots not an MIS-2 */
   MIS2_ERR_TIMEOUT = -5,       /* a device-side barrier gave up after spin_limit polls */
-  MIS2_ERR_NO_PROGRESS = -6    /* round cap (n + 1 rounds) reached */
+  MIS2_ERR_NO_PROGRESS = -6,   /* round cap (n + 1 rounds) reached */
+  MIS2_ERR_CANCELLED = -7      /* serving: the request was cancelled before it started */
 } mis2_status;
 
 /* Aggregation modes. */
@@ -407,6 +408,11 @@ int mis2_server_destroy(mis2_server* s);
 int mis2_server_submit(mis2_server* s, const mis2_csr* g_host, uint64_t seed, int64_t* ticket);
 /* Block until request `ticket` completes; *out (host) receives its result. */
 int mis2_server_wait(mis2_server* s, int64_t ticket, mis2_result* out);
+/* Withdraw request `ticket` if it is still queued: *cancelled (host) = 1 and
+ * its result (mis2_server_wait) has status MIS2_ERR_CANCELLED; a request
+ * already running or finished is left alone (*cancelled = 0).  Does not
+ * block on the GPU.  MIS2_ERR_INVALID_ARG for an unknown ticket. */
+int mis2_server_cancel(mis2_server* s, int64_t ticket, int32_t* cancelled);
 /* Replay an arrival trace: request i (graph pool_host[pool_index[i]])
  * arrives arrival_s[i] seconds after the call starts; results[i] (host)
  * receive the outcomes, *max_in_flight the peak number of concurrent

@@ -313,6 +313,7 @@ int mis2_get_stats(const mis2_ctx* c, mis2_stats* out) {
 
 int mis2_run(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int32_t* roots, int64_t* n_roots,
              int32_t* n_rounds, void* stream) {
+  NvtxRange nvtx_call("mis2_run");
   if (c == nullptr || n_roots == nullptr) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -331,6 +332,7 @@ int mis2_run(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int
 
 int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
                              uint8_t* in_set, int32_t* roots, int64_t* n_roots, int32_t* n_rounds, void* stream) {
+  NvtxRange nvtx_call("mis2_run_with_priorities");
   if (c == nullptr || n_roots == nullptr || table_rounds < 0 || (table_rounds > 0 && prio_table == nullptr) ||
       tuple_ablation(c))
     return MIS2_ERR_INVALID_ARG;
@@ -363,6 +365,7 @@ int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* pri
 
 int mis2_aggregate(mis2_ctx* c, const mis2_csr* g, const int32_t* roots, int64_t n_roots, uint64_t seed,
                    int32_t mode, int32_t* labels, int64_t* n_aggs, void* stream) {
+  NvtxRange nvtx_call("mis2_aggregate");
   if (c == nullptr || n_aggs == nullptr || (mode != MIS2_AGG_ALG3 && mode != MIS2_AGG_BASIC) || tuple_ablation(c))
     return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
@@ -385,6 +388,7 @@ int mis2_aggregate(mis2_ctx* c, const mis2_csr* g, const int32_t* roots, int64_t
 
 int mis2_coarsen(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                  int32_t* c_colind, int64_t c_colind_cap, int64_t* c_nnz, void* stream) {
+  NvtxRange nvtx_call("mis2_coarsen");
   if (c == nullptr || c_nnz == nullptr || c_rowptr == nullptr) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -421,9 +425,15 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
   Scratch& s = c->s;
   const PrioCfg p = make_prio(c, ga.n, seed);
   MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
-  MIS2_TRY(mis2_rounds_device_async(c, ga, nullptr, p, 0, kCtrRounds, st));
-  MIS2_TRY(extract_in_set(c, ga.n, in_set, rl, s.ctr + kCtrRoots, st));
-  MIS2_TRY(agg_level_async(c, ga, rl, p, c->cfg.agg_mode, lab, st));
+  {
+    NvtxRange r("MIS-2 (Algorithm 1)");
+    MIS2_TRY(mis2_rounds_device_async(c, ga, nullptr, p, 0, kCtrRounds, st));
+    MIS2_TRY(extract_in_set(c, ga.n, in_set, rl, s.ctr + kCtrRoots, st));
+  }
+  {
+    NvtxRange r("aggregation (Algorithm 3)");
+    MIS2_TRY(agg_level_async(c, ga, rl, p, c->cfg.agg_mode, lab, st));
+  }
   MIS2_CUDA(cudaMemcpyAsync(c->h_trace, s.dtrace, 2 * MIS2_TRACE_CAP * 4 * sizeof(int64_t), cudaMemcpyDeviceToHost,
                             st));
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -442,6 +452,7 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
     memcpy(c->stats.trace2, c->h_trace + MIS2_TRACE_CAP * 4, sizeof(c->stats.trace2));
   int64_t cn = 0;
   if (c_rowptr != nullptr) {
+    NvtxRange r("coarse graph");
     MIS2_TRY(coarsen_fast(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, st));
     MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MIS2_CUDA(cudaStreamSynchronize(st));
@@ -485,6 +496,7 @@ static int level_impl(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
 int mis2_coarsen_level(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int32_t* roots,
                        int32_t* labels, int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap, int64_t* n_roots,
                        int64_t* n_aggs, int64_t* c_nnz, void* stream) {
+  NvtxRange nvtx_call("mis2_coarsen_level");
   if (c == nullptr || tuple_ablation(c)) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -520,6 +532,7 @@ static int ensure_stage(mis2_ctx* c, int64_t n, int64_t nnz) {
 int mis2_coarsen_level_host(mis2_ctx* c, const mis2_csr* gh, uint64_t seed, uint8_t* in_set, int32_t* roots,
                             int32_t* labels, int32_t* c_rowptr, int32_t* c_colind, int64_t c_colind_cap,
                             int64_t* n_roots, int64_t* n_aggs, int64_t* c_nnz, void* stream) {
+  NvtxRange nvtx_call("mis2_coarsen_level_host");
   if (c == nullptr || gh == nullptr || tuple_ablation(c)) return MIS2_ERR_INVALID_ARG;
   if (gh->n < 0 || gh->nnz < 0 || gh->rowptr == nullptr || (gh->nnz > 0 && gh->colind == nullptr))
     return MIS2_ERR_INVALID_ARG;
@@ -559,6 +572,7 @@ int mis2_coarsen_level_host(mis2_ctx* c, const mis2_csr* gh, uint64_t seed, uint
 
 int mis2_run_k(mis2_ctx* c, const mis2_csr* g, int32_t k, uint64_t seed, uint8_t* in_set, int32_t* roots,
                int64_t* n_roots, int32_t* n_rounds, void* stream) {
+  NvtxRange nvtx_call("mis2_run_k");
   if (c == nullptr || n_roots == nullptr || k < 1 || k > 16) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -572,6 +586,7 @@ int mis2_run_k(mis2_ctx* c, const mis2_csr* g, int32_t k, uint64_t seed, uint8_t
 
 int mis2_color(mis2_ctx* c, const mis2_csr* g, uint64_t seed, int32_t* colors, int32_t* color_ptr,
                int32_t* color_list, int32_t* n_colors, int32_t* n_rounds, void* stream) {
+  NvtxRange nvtx_call("mis2_color");
   if (c == nullptr || n_colors == nullptr || color_ptr == nullptr) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -586,6 +601,7 @@ int mis2_color(mis2_ctx* c, const mis2_csr* g, uint64_t seed, int32_t* colors, i
 int mis2_coarse_weights(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, int64_t n_aggs,
                         const int32_t* c_rowptr, const int32_t* c_colind, int64_t c_nnz, int32_t* c_weights,
                         void* stream) {
+  NvtxRange nvtx_call("mis2_coarse_weights");
   if (c == nullptr || c_rowptr == nullptr) return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -602,6 +618,7 @@ int mis2_coarse_weights(mis2_ctx* c, const mis2_csr* g, const int32_t* labels, i
 
 int mis2_tentative_prolongator(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int32_t normalize,
                                int32_t* p_rowptr, int32_t* p_colind, double* p_values, void* stream) {
+  NvtxRange nvtx_call("mis2_tentative_prolongator");
   if (c == nullptr || n < 0 || n > c->max_n || n_aggs < 0 || n_aggs > n || p_rowptr == nullptr ||
       (n > 0 && (labels == nullptr || p_colind == nullptr || p_values == nullptr)))
     return MIS2_ERR_INVALID_ARG;
@@ -613,6 +630,7 @@ int mis2_tentative_prolongator(mis2_ctx* c, const int32_t* labels, int64_t n, in
 
 int mis2_cluster_lists(mis2_ctx* c, const int32_t* labels, int64_t n, int64_t n_aggs, int32_t* c_ptr,
                        int32_t* members, void* stream) {
+  NvtxRange nvtx_call("mis2_cluster_lists");
   if (c == nullptr || n < 0 || n > c->max_n || n_aggs < 0 || n_aggs > n || (n > 0 && n_aggs == 0) ||
       c_ptr == nullptr || (n > 0 && (labels == nullptr || members == nullptr)))
     return MIS2_ERR_INVALID_ARG;
@@ -634,6 +652,7 @@ const char* mis2_status_string(int status) {
     case MIS2_ERR_BAD_GRAPH: return "MIS2_ERR_BAD_GRAPH";
     case MIS2_ERR_TIMEOUT: return "MIS2_ERR_TIMEOUT";
     case MIS2_ERR_NO_PROGRESS: return "MIS2_ERR_NO_PROGRESS";
+    case MIS2_ERR_CANCELLED: return "MIS2_ERR_CANCELLED";
     default: return "MIS2_ERR_UNKNOWN";
   }
 }

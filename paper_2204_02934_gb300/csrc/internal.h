@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -12,6 +13,16 @@
 #include "common.cuh"
 
 namespace mis2 {
+
+// A named range on a profiler's NVTX timeline (ncu --nvtx filters kernels by
+// it): pushed for the scope, popped at its end; without a profiler attached
+// the calls do nothing.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ------------------------------------------------------------- counter words
 // Worklist sizes rotate over three slots per round r: input slot r%3, output

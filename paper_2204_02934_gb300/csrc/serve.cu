@@ -279,6 +279,32 @@ int mis2_server_wait(mis2_server* s, int64_t ticket, mis2_result* out) {
   return MIS2_OK;
 }
 
+int mis2_server_cancel(mis2_server* s, int64_t ticket, int32_t* cancelled) {
+  if (s == nullptr || cancelled == nullptr) return MIS2_ERR_INVALID_ARG;
+  *cancelled = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (ticket < 0 || ticket >= s->next_ticket) return MIS2_ERR_INVALID_ARG;
+    auto it = std::find_if(s->queue.begin(), s->queue.end(), [&](const Request& r) { return r.ticket == ticket; });
+    if (it == s->queue.end()) return MIS2_OK;  // running or finished: its result stands
+    mis2_result res{};
+    res.ticket = ticket;
+    res.n = it->g.n;
+    res.nnz = it->g.nnz;
+    res.t_arrive = secs(s, it->t_arrive);
+    res.t_start = res.t_done = secs(s, Clock::now());
+    res.status = MIS2_ERR_CANCELLED;
+    res.slot = -1;
+    s->queue.erase(it);
+    s->done[ticket] = res;
+    s->finished[ticket] = 1;
+    *cancelled = 1;
+  }
+  s->cv_work.notify_all();  // the new queue head may fit the budget
+  s->cv_done.notify_all();
+  return MIS2_OK;
+}
+
 int mis2_server_replay(mis2_server* s, int32_t n_pool, const mis2_csr* pool_host, int64_t n_req,
                        const double* arrival_s, const int32_t* pool_index, uint64_t seed, mis2_result* results,
                        int64_t* max_in_flight) {

@@ -39,7 +39,7 @@ EXPORTS = [
     "mis2_batch_create", "mis2_batch_destroy", "mis2_batch_coarsen", "mis2_batch_level_sizes", "mis2_batch_labels",
     "mis2_batch_coarse", "mis2_batch_stats",
     "mis2_server_config_default", "mis2_server_create", "mis2_server_destroy", "mis2_server_submit",
-    "mis2_server_wait", "mis2_server_replay", "mis2_coarse_weights", "mis2_tentative_prolongator",
+    "mis2_server_wait", "mis2_server_cancel", "mis2_server_replay", "mis2_coarse_weights", "mis2_tentative_prolongator",
     "mis2_run_k", "mis2_color", "mis2_cluster_lists",
 ]
 MIS2_NOALLOC_MAX_N = 262144
@@ -140,6 +140,7 @@ def _lib(build_if_missing: bool = False):
         "mis2_server_destroy": (i32, [P]),
         "mis2_server_submit": (i32, [P, CSR, u64, pi64]),
         "mis2_server_wait": (i32, [P, i64, ctypes.POINTER(mis2_result)]),
+        "mis2_server_cancel": (i32, [P, i64, pi32]),
         "mis2_server_replay": (i32, [P, i32, CSR, i64, P, P, u64, ctypes.POINTER(mis2_result), pi64]),
         "mis2_coarse_weights": (i32, [P, CSR, P, i64, P, P, i64, P, P]),
         "mis2_run_k": (i32, [P, CSR, i32, u64, P, P, pi64, pi32, P]),
@@ -598,6 +599,13 @@ def mis2_server_wait(s, ticket: int) -> mis2_result:
     return r
 
 
+def mis2_server_cancel(s, ticket: int) -> bool:
+    """True if the request was still queued and is now withdrawn."""
+    c = ctypes.c_int32(0)
+    _check(_lib().mis2_server_cancel(s, ticket, ctypes.byref(c)), "mis2_server_cancel")
+    return bool(c.value)
+
+
 def mis2_server_replay(s, pool, arrival_s, pool_index, seed: int = 0):
     """pool: list of host mis2_csr.  Returns (list of mis2_result, max in flight)."""
     arr = (mis2_csr * len(pool))(*pool)
@@ -634,3 +642,13 @@ class Server:
 
     def replay(self, pool_host, arrival_s, pool_index, seed: int = 0):
         return mis2_server_replay(self.handle, pool_host, arrival_s, pool_index, seed)
+
+    def submit(self, g_host: mis2_csr, seed: int = 0) -> int:
+        """Queue one request (g_host must stay valid until it completes)."""
+        return mis2_server_submit(self.handle, g_host, seed)
+
+    def wait(self, ticket: int) -> mis2_result:
+        return mis2_server_wait(self.handle, ticket)
+
+    def cancel(self, ticket: int) -> bool:
+        return mis2_server_cancel(self.handle, ticket)

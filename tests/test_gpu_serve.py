@@ -112,3 +112,26 @@ def test_oversize_request_is_refused():
         mis2.mis2_server_submit(srv.handle, host[3], 0)
     assert e.value.status == -2
     srv.close()
+
+
+def test_cancel_withdraws_queued_requests_only():
+    # one slot: the first request runs, the others queue behind it; every
+    # cancelled one reports MIS2_ERR_CANCELLED, every other one the oracle's
+    # result, and a finished request cannot be cancelled
+    graphs, keep, host = _pool()
+    big = int(np.argmax([g.nnz for g in graphs]))
+    expect = _oracle_checksum(graphs[big], 5)[0]
+    srv = mis2.Server(slots=1, slot_max_n=20000, slot_max_nnz=200000)
+    tickets = [srv.submit(host[big], 5) for _ in range(24)]
+    cancelled = {t: srv.cancel(t) for t in tickets[8:]}
+    assert any(cancelled.values()), "the tail of a 24-deep queue behind one slot was still queued"
+    for t in tickets:
+        r = srv.wait(t)
+        if cancelled.get(t):
+            assert r.status == -7 and r.slot == -1
+        else:
+            assert r.status == 0 and r.checksum == expect
+    assert not srv.cancel(tickets[0])  # finished: nothing to withdraw
+    with pytest.raises(mis2.Mis2Error):
+        srv.cancel(10_000)  # unknown ticket
+    srv.close()
