@@ -33,13 +33,15 @@ constexpr int kColorBatch = 8;
 constexpr int kScanU = 4;  // entries a lane tests per step of the blocked scan
 
 __global__ void __launch_bounds__(kBlock) k_color_init(int64_t n, PrioCfg p, uint32_t* prio, int32_t* col,
-                                                       int32_t* when, int32_t* resume) {
+                                                       int32_t* when, int32_t* resume, uint32_t* mlo, uint32_t* mhi) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
     prio[v] = make_tuple(p, 0u, (uint32_t)v);
     col[v] = -1;
     when[v] = kUncolored;
     resume[v] = 0;
+    mlo[v] = 0u;
+    mhi[v] = 0u;
   }
 }
 
@@ -51,12 +53,17 @@ __device__ __forceinline__ bool blocks_v(int32_t w, int64_t v, uint32_t pv, cons
 }
 
 // One Jones-Plassmann round over the short rows, G lanes per uncoloured
-// vertex.  A vertex whose neighbours use every colour of the first window
-// of 64 looks at the next window.
+// vertex.  The blocked scan also collects the colours (below 64) of the
+// neighbours it finds coloured: a neighbour coloured before v has the
+// smaller tuple (a larger one waits for v), so its colour is final and
+// belongs to v's first-fit mask, kept per vertex (mlo / mhi) across rounds.
+// When v is no longer blocked its mask is complete, and it takes the first
+// free colour without a second pass over the row; only a vertex whose
+// neighbours use all of 0..63 walks the row again, window by window.
 template <int G, bool PACK, typename I>
 __device__ __forceinline__ void color_light_pass(const GraphView<I>& g, int64_t light_max, const uint32_t* prio,
-                                                 int32_t* col, int32_t* when, int32_t* resume, int32_t round,
-                                                 int32_t* left, int32_t* max_color) {
+                                                 int32_t* col, int32_t* when, int32_t* resume, uint32_t* mlo,
+                                                 uint32_t* mhi, int32_t round, int32_t* left, int32_t* max_color) {
   const int lg = lane_id() & (G - 1);
   int32_t still = 0;
   for_picked<G, PACK>(
@@ -76,29 +83,55 @@ __device__ __forceinline__ void color_light_pass(const GraphView<I>& g, int64_t 
         // a smaller uncoloured neighbour, from the resume point on; stop at
         // the first chunk that holds one
         bool blocked = false;
+        uint32_t lo = 0, hi = 0;  // colours of the coloured neighbours met
         for (int32_t off = res;; off += G * kScanU) {
           const bool live = active && !blocked && off < len;
           if (!__any_sync(kFull, live)) break;
           bool h = false;
           if (live) {
-            int32_t w[kScanU];  // all loads of the step first, then the tests
+            int32_t w[kScanU], tw[kScanU];  // all loads of the step first, then the tests
 #pragma unroll
             for (int u = 0; u < kScanU; u++) {
               const int32_t q = off + lg + u * G;
-              w[u] = q < len ? __ldg(g.colind + s + q) : (int32_t)v;  // v itself never blocks
+              w[u] = q < len ? __ldg(g.colind + s + q) : (int32_t)v;  // v itself neither blocks nor counts
             }
 #pragma unroll
-            for (int u = 0; u < kScanU; u++) h |= blocks_v(w[u], v, pv, prio, when, round);
+            for (int u = 0; u < kScanU; u++) tw[u] = w[u] != v ? when[w[u]] : kUncolored;
+#pragma unroll
+            for (int u = 0; u < kScanU; u++) {
+              if (w[u] == v) continue;
+              if (tw[u] < round) {
+                const int32_t cw = col[w[u]];
+                if (cw < 32) lo |= 1u << cw;
+                else if (cw < 64) hi |= 1u << (cw - 32);
+              } else if (prio[w[u]] < pv) {
+                h = true;
+              }
+            }
           }
           if (group_any<G>(h) && live) {
             blocked = true;
             res = off;
           }
         }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+          lo |= __shfl_xor_sync(kFull, lo, o);
+          hi |= __shfl_xor_sync(kFull, hi, o);
+        }
+        if (active) {
+          lo |= mlo[v];
+          hi |= mhi[v];
+        }
         const bool mine = active && !blocked;
         int32_t c = -1;
+        if (mine) {
+          if (~lo != 0u) c = __ffs(~lo) - 1;
+          else if (~hi != 0u) c = 32 + __ffs(~hi) - 1;
+        }
+        // colours from 64 on (rare): the row again, a window of 64 at a time;
         // warp-uniform trip count: every lane takes part in the group reductions
-        for (int32_t wbase = 0; __any_sync(kFull, mine && c < 0); wbase += 64) {
+        for (int32_t wbase = 64; __any_sync(kFull, mine && c < 0); wbase += 64) {
           uint32_t lo = 0, hi = 0;
           if (mine && c < 0)
             for (int32_t off = lg; off < len; off += G) {
@@ -126,6 +159,8 @@ __device__ __forceinline__ void color_light_pass(const GraphView<I>& g, int64_t 
             atomicMax(max_color, c);
           } else if (active) {
             resume[v] = res;
+            mlo[v] = lo;
+            mhi[v] = hi;
             still++;
           }
         }
@@ -136,9 +171,10 @@ __device__ __forceinline__ void color_light_pass(const GraphView<I>& g, int64_t 
 
 template <int G, bool PACK, typename I>
 __global__ void __launch_bounds__(kBlock) k_color_round(GraphView<I> g, int64_t light_max, const uint32_t* prio,
-                                                        int32_t* col, int32_t* when, int32_t* resume, int32_t round,
-                                                        int32_t* left, int32_t* max_color) {
-  color_light_pass<G, PACK, I>(g, light_max, prio, col, when, resume, round, left, max_color);
+                                                        int32_t* col, int32_t* when, int32_t* resume, uint32_t* mlo,
+                                                        uint32_t* mhi, int32_t round, int32_t* left,
+                                                        int32_t* max_color) {
+  color_light_pass<G, PACK, I>(g, light_max, prio, col, when, resume, mlo, mhi, round, left, max_color);
 }
 
 // One listed row with a team of TPR threads (a warp or the block): the
@@ -248,7 +284,8 @@ __global__ void __launch_bounds__(kBlock) k_color_heavy(GraphView<I> g, const in
 // the slot zeroed in round r was last read right after barrier r - 1.
 template <int G, bool PACK, typename I>
 __global__ void __launch_bounds__(kBlock) k_color_loop(GraphView<I> g, int64_t light_max, const uint32_t* prio,
-                                                       int32_t* col, int32_t* when, int32_t* resume,
+                                                       int32_t* col, int32_t* when, int32_t* resume, uint32_t* mlo,
+                                                       uint32_t* mhi,
                                                        const int32_t* medium, const int32_t* n_medium,
                                                        const int32_t* heavy, const int32_t* n_heavy, int32_t* ctr,
                                                        int32_t* max_color, int64_t spin_limit, int32_t max_rounds,
@@ -261,7 +298,7 @@ __global__ void __launch_bounds__(kBlock) k_color_loop(GraphView<I> g, int64_t l
   int32_t r = 0;
   for (;; r++) {
     int32_t* lr = left + r % 3;
-    color_light_pass<G, PACK, I>(g, light_max, prio, col, when, resume, r, lr, max_color);
+    color_light_pass<G, PACK, I>(g, light_max, prio, col, when, resume, mlo, mhi, r, lr, max_color);
     if (nm > 0) color_medium_pass<I>(g, medium, nm, prio, col, when, resume, r, lr, max_color);
     if (nh > 0) color_heavy_pass<I>(g, heavy, nh, prio, col, when, resume, r, lr, max_color, sh);
     if (!grid_barrier(ctr + kCtrBarrier, epoch, ctr + kCtrErr, spin_limit, nullptr, barrier_extra)) return;
@@ -289,11 +326,13 @@ int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, con
   uint32_t* prio = s.M;
   int32_t* when = s.tent;
   int32_t* resume = s.members;
+  uint32_t* mlo = reinterpret_cast<uint32_t*>(s.ub);  // first-fit masks of the short rows
+  uint32_t* mhi = reinterpret_cast<uint32_t*>(s.ub_ptr);
   int32_t* left = s.ctr + kCtrColorLeft;
   int32_t* maxc = s.ctr + kCtrM2;
   MIS2_CUDA(cudaMemsetAsync(maxc, 0xFF, sizeof(int32_t), st));
   const int rb = grid_for(c, gv.n, kBlock);
-  k_color_init<<<rb, kBlock, 0, st>>>(gv.n, p, prio, colors, when, resume);
+  k_color_init<<<rb, kBlock, 0, st>>>(gv.n, p, prio, colors, when, resume, mlo, mhi);
   c->launches++;
   // packed walk (a warp per 32 vertices) once the graph fills the machine
   const bool pack = gv.n > (int64_t)c->sm_count * 2048;
@@ -306,30 +345,38 @@ int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, con
     int per_sm = 0;
     MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
     if (per_sm < 1) return MIS2_ERR_CUDA;
-    const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 4;
+    const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 6;
     const int blocks = c->sm_count * std::min(per_sm, want);
     MIS2_CUDA(cudaMemsetAsync(left, 0, 3 * sizeof(int32_t), st));
     MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrBarrier, 0, sizeof(int32_t), st));
     MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrErr, 0, sizeof(int32_t), st));
-    GraphView<I> g = gv;
-    int64_t lm = light_max;
-    const int32_t* med = rl.medium;
-    const int32_t* nmed = rl.n_medium_dev;
-    const int32_t* hv = rl.heavy;
-    const int32_t* nhv = rl.n_heavy_dev;
-    int32_t* ctr = s.ctr;
-    int64_t spin = c->cfg.spin_limit;
-    int32_t max_rounds = (int32_t)std::min<int64_t>(gv.n, (int64_t)1 << 30);
-    int32_t extra = (c->cfg.debug_checks & MIS2_DEBUG_FORCE_TIMEOUT) ? 1 : 0;  // test hook: the waits run out
-    void* args[] = {&g,   &lm,  &prio, &colors, &when, &resume, &med,        &nmed,
-                    &hv,  &nhv, &ctr,  &maxc,   &spin, &max_rounds, &extra};
+    const int64_t spin = c->cfg.spin_limit;
+    const int32_t max_rounds = (int32_t)std::min<int64_t>(gv.n, (int64_t)1 << 30);
+    const int32_t extra = (c->cfg.debug_checks & MIS2_DEBUG_FORCE_TIMEOUT) ? 1 : 0;  // test hook: the waits run out
+    // cooperative launch through the typed form: the arguments are checked
+    // against the kernel's parameters at compile time
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(blocks);
+    lc.blockDim = dim3(kBlock);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = st;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    auto launch = [&]() {
+      return cudaLaunchKernelEx(&lc, kern, gv, light_max, (const uint32_t*)prio, colors, when, resume, mlo, mhi,
+                                (const int32_t*)rl.medium, rl.n_medium_dev, (const int32_t*)rl.heavy, rl.n_heavy_dev,
+                                s.ctr, maxc, spin, max_rounds, extra);
+    };
     if (c->coop_lock != nullptr) {
       std::lock_guard<std::mutex> lk(*c->coop_lock);
-      MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+      MIS2_CUDA(launch());
       MIS2_CUDA(cudaEventRecord(c->coop_done, st));
       MIS2_CUDA(cudaEventSynchronize(c->coop_done));
     } else {
-      MIS2_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(kBlock), args, 0, st));
+      MIS2_CUDA(launch());
     }
     c->launches++;
     MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -345,11 +392,11 @@ int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, con
     MIS2_CUDA(cudaMemsetAsync(left, 0, kColorBatch * sizeof(int32_t), st));
     for (int b = 0; b < kColorBatch; b++) {
       if (pack)
-        k_color_round<G, true, I><<<wb, kBlock, 0, st>>>(gv, light_max, prio, colors, when, resume, r0 + b,
-                                                          left + b, maxc);
+        k_color_round<G, true, I><<<wb, kBlock, 0, st>>>(gv, light_max, prio, colors, when, resume, mlo, mhi,
+                                                          r0 + b, left + b, maxc);
       else
-        k_color_round<G, false, I><<<wb, kBlock, 0, st>>>(gv, light_max, prio, colors, when, resume, r0 + b,
-                                                           left + b, maxc);
+        k_color_round<G, false, I><<<wb, kBlock, 0, st>>>(gv, light_max, prio, colors, when, resume, mlo, mhi,
+                                                           r0 + b, left + b, maxc);
       c->launches++;
       if (mb > 0) {
         k_color_medium<I><<<mb, kBlock, 0, st>>>(gv, rl.medium, rl.n_medium_dev, prio, colors, when, resume, r0 + b,
