@@ -64,3 +64,20 @@ def test_debug_bits_match_the_header():
         m = re.search(r"#define\s+" + name + r"\s+(0x[0-9a-fA-F]+|\d+)", hdr)
         assert m, name
         assert int(m.group(1), 0) == getattr(mis2, name)
+
+
+def test_every_status_code_has_a_name():
+    hdr = open(os.path.join(ROOT, "include", "mis2.h")).read()
+    codes = dict((name, int(val)) for name, val in re.findall(r"(MIS2_(?:OK|ERR_[A-Z_]+))\s*=\s*(-?\d+)", hdr))
+    assert "MIS2_ERR_CANCELLED" in codes and len(codes) >= 8
+    for name, val in codes.items():
+        assert mis2.mis2_status_string(val) == name
+    assert mis2.mis2_status_string(-99) == "MIS2_ERR_UNKNOWN"
+
+
+def test_ablation_bits_match_the_header():
+    hdr = open(os.path.join(ROOT, "include", "mis2.h")).read()
+    for name in ("MIS2_ABLATE_NO_WORKLISTS", "MIS2_ABLATE_TUPLE_ENGINE", "MIS2_ABLATE_UNPACKED_TUPLES"):
+        m = re.search(r"#define\s+" + name + r"\s+(0x[0-9a-fA-F]+|\d+)", hdr)
+        assert m, name
+        assert int(m.group(1), 0) == getattr(mis2, name)
