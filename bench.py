@@ -628,7 +628,8 @@ def run_setup(args):
     rows = []
     for gname, g in graphs:
         dg = mis2.DeviceGraph.from_host(g)
-        ctx = mis2.Context(g.n, g.nnz, loop=mis2.MIS2_LOOP_DEVICE)
+        ctx = mis2.Context(g.n, g.nnz, loop=mis2.MIS2_LOOP_DEVICE if args.loop == "device" else
+                           mis2.MIS2_LOOP_HOST)
         lv = ctx.coarsen_level(dg, 0)
         labels, na = lv["labels"], int(lv["n_aggs"])
         crp, cci = lv["c_rowptr"], lv["c_colind"]
@@ -698,7 +699,8 @@ def run_setup(args):
     line = {"metric": "setup steps after the coarse graph on GB300 (time per call)", "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
             "config": {"workload": "27-point 100^3 grid and R-MAT scale 20 (seed 42), level-0 aggregation, seed 0",
-                       "steps": args.steps, "l2": "flushed (256 MiB write) before each timed call"},
+                       "loop": args.loop, "steps": args.steps,
+                       "l2": "flushed (256 MiB write) before each timed call"},
             "rows": rows}
     print(json.dumps(line), flush=True)
     return 0
