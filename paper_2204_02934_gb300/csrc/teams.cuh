@@ -25,18 +25,19 @@ __device__ __forceinline__ void for_picked(int64_t n, Pick&& pick, Body&& body) 
       const int64_t v = base + sub;
       body(v < n && pick(v) ? v : (int64_t)-1);
     }
-    return;
-  }
-  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nw * 32) {
-    const int64_t vl = base + lane;
-    unsigned mask = __ballot_sync(kFull, vl < n && pick(vl));
-    while (mask != 0u) {  // warp-uniform
-      unsigned mm = mask;
-      for (int i = 0; i < sub; i++) mm &= mm - 1u;
-      const int64_t v = mm != 0u ? base + __ffs(mm) - 1 : -1;
+  } else {
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n;
+         base += nw * 32) {
+      const int64_t vl = base + lane;
+      unsigned mask = __ballot_sync(kFull, vl < n && pick(vl));
+      while (mask != 0u) {  // warp-uniform
+        unsigned mm = mask;
+        for (int i = 0; i < sub; i++) mm &= mm - 1u;
+        const int64_t v = mm != 0u ? base + __ffs(mm) - 1 : -1;
 #pragma unroll
-      for (int i = 0; i < RPW; i++) mask &= mask - 1u;
-      body(v);
+        for (int i = 0; i < RPW; i++) mask &= mask - 1u;
+        body(v);
+      }
     }
   }
 }
