@@ -62,8 +62,13 @@ typedef enum {
 /* Aggregation modes. */
 enum { MIS2_AGG_ALG3 = 0, MIS2_AGG_BASIC = 1 };
 
-/* Priority hash variants (Section V-A, Table I).  XORSHIFT_STAR is the
- * paper's choice and the default; the others exist for the ablation. */
+/* Priority hash variants (Section V-A, Table I): h(iter, v) = f(f(iter) ^
+ * f(v) ^ seed).  XORSHIFT_STAR (the paper's choice and the default): f =
+ * xorshift64*, shifts 12/25/27 then a multiply by 0x2545F4914F6CDD1D.
+ * XORSHIFT: the same shifts without the multiply.  FIXED: xorshift64* with
+ * iter held at 0 (priorities drawn once).  The priority of Eq. 1 is the
+ * hash truncated to the 32-bit status word, shifted left by b: its low
+ * 32 - b bits. */
 enum { MIS2_HASH_XORSHIFT_STAR = 0, MIS2_HASH_XORSHIFT = 1, MIS2_HASH_FIXED = 2 };
 
 /* Round-loop drivers: HOST reads the worklist size back after every round
@@ -128,8 +133,8 @@ typedef struct {
  * MIS2_ABLATE_UNPACKED_TUPLES: the same engine with the status tuple left
  *   unpacked (Section V-C's packing measured against, Fig. 2): status,
  *   priority and vertex id in separate arrays, compared field by field, the
- *   priority being the top 32 bits of h(iter, v) (Eq. 1 keeps 32 - b), so
- *   ties the packing breaks by id may go the other way.
+ *   priority being the 32 - b bits Eq. 1 packs: the same order, so the same
+ *   MIS-2 as the packed engine and mis2_run.
  * Both apply to mis2_run alone: mis2_run_with_priorities, mis2_aggregate,
  * mis2_coarsen_level(_host) and mis2_batch_create refuse a configuration
  * with either set (MIS2_ERR_INVALID_ARG). */

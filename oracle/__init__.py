@@ -80,6 +80,8 @@ def _load():
             lib.oracle_id_bits.restype = i32
             lib.oracle_pack.argtypes = [u64, i64, i32]
             lib.oracle_pack.restype = ctypes.c_uint32
+            lib.oracle_hash.argtypes = [i32, u64, i64, u64]
+            lib.oracle_hash.restype = ctypes.c_uint64
             lib.oracle_priority_tuple.argtypes = [i32, u64, i64, i64, u64]
             lib.oracle_priority_tuple.restype = ctypes.c_uint32
             _lib = lib
@@ -107,6 +109,11 @@ def id_bits(n: int) -> int:
 
 def pack(hash64: int, v: int, b: int) -> int:
     return int(_load().oracle_pack(hash64, v, b))
+
+
+def hash64(iter_: int, v: int, seed: int = 0, hash_variant: int = 0) -> int:
+    """h(iter, v) = f(f(iter) ^ f(v) ^ seed) of Section V-A, all 64 bits."""
+    return int(_load().oracle_hash(hash_variant, iter_, v, seed))
 
 
 def priority_tuple(iter_: int, v: int, n: int, seed: int = 0, hash_variant: int = 0) -> int:
@@ -196,7 +203,8 @@ def misk(g, k: int, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
 
 def mis2_unpacked(g, seed: int = 0, hash_variant: int = HASH_XORSHIFT_STAR):
     """Algorithm 1 with unpacked (status, priority, id) tuples, priority =
-    the top 32 hash bits.  Returns (in_set uint8[n], roots int32, rounds)."""
+    the 32-b bits Eq. 1 packs.  Returns (in_set uint8[n], roots int32,
+    rounds)."""
     lib = _load()
     n, rp, ci = _csr(g)
     in_set = np.zeros(max(n, 1), dtype=np.uint8)

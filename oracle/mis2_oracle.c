@@ -41,9 +41,13 @@
  *   - decide: "if some M_w = OUT then OUT, else if every M_w = T_v then IN",
  *     both tests on the tuple T_v held before the step (Fig. 1, round 2).
  *   - f is xorshift64* (Vigna 2016: shifts 12, 25, 27, multiplier
- *     0x2545F4914F6CDD1D); the priority is the top 32-b bits of the 64-bit
- *     hash; a caller seed is xored into the inner term (seed 0 = the
- *     paper's formula).  iter restarts at 0 for every MIS-2.
+ *     0x2545F4914F6CDD1D); Table I's plain "Xor" hash is the same xorshift
+ *     stage without the multiply (Section V-A describes xorshift* as
+ *     xorshift followed by a linear congruential step).  Eq. 1's
+ *     (priority << b) | (id + 1) is evaluated in the 32-bit status word,
+ *     so the priority is the hash truncated to 32 bits whose low 32-b bits
+ *     survive the shift.  A caller seed is xored into the inner term (seed
+ *     0 = the paper's formula).  iter restarts at 0 for every MIS-2.
  *   - phase 2 runs MIS-2 on the subgraph induced by the unaggregated
  *     vertices, in the original numbering (b from the full n); other
  *     vertices are absent from it (neither relay nor block).
@@ -83,12 +87,13 @@ static uint64_t orc_xorshift_star(uint64_t x) {
   return x * 2685821657736338717ull;
 }
 
-/* Plain 64-bit xorshift, Marsaglia's (13, 7, 17) triple (J. Stat. Softw. 8,
- * 2003): the "Xor Hash" column of Table I. */
+/* Plain 64-bit xorshift: the xorshift stage of xorshift64* above without
+ * its multiplicative step (Section V-A: xorshift* is xorshift followed by a
+ * linear congruential step), the "Xor Hash" column of Table I. */
 static uint64_t orc_xorshift(uint64_t x) {
-  x ^= x << 13;
-  x ^= x >> 7;
-  x ^= x << 17;
+  x ^= x >> 12;
+  x ^= x << 25;
+  x ^= x >> 27;
   return x;
 }
 
@@ -107,11 +112,21 @@ int oracle_id_bits(int64_t n) {
   return b;
 }
 
-/* Eq. 1 packing: (priority << b) | (id + 1), priority = top 32-b hash bits. */
+/* Eq. 1 packing in the 32-bit status word: (priority << b) | (id + 1) with
+ * priority = the hash truncated to 32 bits, so its low 32-b bits remain. */
+uint32_t oracle_priority_bits(uint64_t hash, int b) {
+  if (b >= 32) return 0u;
+  return (uint32_t)(hash & ((((uint64_t)1) << (32 - b)) - 1u));
+}
+
 uint32_t oracle_pack(uint64_t hash, int64_t v, int b) {
-  uint32_t prio = b >= 32 ? 0u : (uint32_t)(hash >> (32 + b));
-  uint32_t hi = b >= 32 ? 0u : (prio << b);
+  uint32_t hi = b >= 32 ? 0u : (oracle_priority_bits(hash, b) << b);
   return hi | (uint32_t)(v + 1);
+}
+
+/* The 64-bit hash h(iter, v) itself (exported for the tests that pin f). */
+uint64_t oracle_hash(int variant, uint64_t iter, int64_t v, uint64_t seed) {
+  return orc_hash(variant, iter, (uint64_t)v, seed);
 }
 
 uint32_t oracle_priority_tuple(int variant, uint64_t iter, int64_t v, int64_t n, uint64_t seed) {
@@ -246,8 +261,10 @@ int oracle_mis2(int64_t n, const int64_t* rowptr, const int32_t* colind, uint64_
 /*
  * Algorithm 1 with the status tuple left unpacked (the variant Section V-C's
  * packing is measured against, Fig. 2): T_v = (status, priority, id) with
- * status IN < UNDECIDED < OUT, priority = the top 32 bits of h(iter, v), id =
- * v, compared field by field.  The round structure is Algorithm 1's: row
+ * status IN < UNDECIDED < OUT, priority = the same 32-b hash bits that Eq. 1
+ * packs (so both forms order undecided vertices alike and reach the same
+ * set: the packing changes the representation, not the result), id = v,
+ * compared field by field.  The round structure is Algorithm 1's: row
  * refresh of the undecided vertices, column = the smallest tuple of the
  * closed neighbourhood with IN turned into OUT, decide = OUT if some
  * neighbour's column tuple is OUT, else IN if every one equals T_v.  Every
@@ -279,6 +296,7 @@ int oracle_mis2_unpacked(int64_t n, const int64_t* rowptr, const int32_t* colind
   orc_tuple* Tn = (orc_tuple*)malloc(sizeof(orc_tuple) * (size_t)(n + 1));
   if (!T || !M || !Tn) { free(T); free(M); free(Tn); return ORC_ERR_NOMEM; }
   const orc_tuple out = {2, 0xFFFFFFFFu, INT64_MAX};
+  const int b = oracle_id_bits(n);
   for (int64_t v = 0; v < n; v++) T[v].status = 1;
   int64_t iter = 0, undecided = n;
   int rc = ORC_OK;
@@ -287,7 +305,7 @@ int oracle_mis2_unpacked(int64_t n, const int64_t* rowptr, const int32_t* colind
     /* refresh row */
     for (int64_t v = 0; v < n; v++)
       if (T[v].status == 1) {
-        T[v].prio = (uint32_t)(orc_hash(hash_variant, (uint64_t)iter, (uint64_t)v, seed) >> 32);
+        T[v].prio = oracle_priority_bits(orc_hash(hash_variant, (uint64_t)iter, (uint64_t)v, seed), b);
         T[v].id = v;
       }
     /* refresh column */

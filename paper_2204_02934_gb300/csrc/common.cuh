@@ -19,9 +19,11 @@ constexpr int kBlock = 256;             // threads of every row kernel
 
 // ----------------------------------------------------------------- priorities
 // f = xorshift64* (Vigna, ACM TOMS 2016: xorshift triple 12/25/27, then a
-// multiply by 0x2545F4914F6CDD1D); the Table I ablation also offers
-// Marsaglia's plain xorshift (13/7/17).  h(iter, v) = f(f(iter) ^ f(v) ^ seed)
-// (Section V-A; seed 0 is the paper's formula).
+// multiply by 0x2545F4914F6CDD1D); the Table I ablation also offers plain
+// xorshift: the same xorshift stage without the multiply (Section V-A calls
+// xorshift* xorshift followed by a linear congruential step).
+// h(iter, v) = f(f(iter) ^ f(v) ^ seed) (Section V-A; seed 0 is the paper's
+// formula).
 __host__ __device__ __forceinline__ uint64_t xorshift_star64(uint64_t x) {
   x ^= x >> 12;
   x ^= x << 25;
@@ -29,9 +31,9 @@ __host__ __device__ __forceinline__ uint64_t xorshift_star64(uint64_t x) {
   return x * 0x2545F4914F6CDD1Dull;
 }
 __host__ __device__ __forceinline__ uint64_t xorshift64(uint64_t x) {
-  x ^= x << 13;
-  x ^= x >> 7;
-  x ^= x << 17;
+  x ^= x >> 12;
+  x ^= x << 25;
+  x ^= x >> 27;
   return x;
 }
 
@@ -52,8 +54,10 @@ struct PrioCfg {
   int32_t pad;
 };
 
-// Section V-C, Eq. 1: (priority << b) | (v + 1) with the top 32 - b hash bits
-// as priority.  2^b >= n + 2 keeps the result away from IN (0) and OUT.
+// Section V-C, Eq. 1: (priority << b) | (v + 1) evaluated in the 32-bit
+// status word, the priority being the hash truncated to 32 bits: its low
+// 32 - b bits survive the shift.  2^b >= n + 2 keeps the result away from
+// IN (0) and OUT.
 __device__ __forceinline__ uint32_t make_tuple(const PrioCfg& p, uint32_t iter, uint32_t v) {
   uint32_t prio;
   int b = p.b;
@@ -72,7 +76,7 @@ __device__ __forceinline__ uint32_t make_tuple(const PrioCfg& p, uint32_t iter, 
       const uint64_t it = p.variant == MIS2_HASH_FIXED ? 0ull : (uint64_t)iter;
       h = xorshift_star64(xorshift_star64(it) ^ xorshift_star64((uint64_t)v) ^ p.seed);
     }
-    prio = b >= 32 ? 0u : (uint32_t)(h >> (32 + b));
+    prio = (uint32_t)h;
   }
   return (b >= 32 ? 0u : (prio << b)) | (v + 1u);
 }

@@ -3,9 +3,10 @@
 // unpacked tuples): host-driven rounds, ordered worklists rebuilt by
 // compaction every round, G lanes per row.  The status tuple is either
 // packed in one 32-bit word (Eq. 1) or unpacked as (status, priority, vertex
-// id) in separate arrays compared field by field, with the top 32 hash bits
-// as priority.  Everything but the tuple is shared, so the two times isolate
-// the packing.  The packed variant computes exactly mis2_run's MIS-2.
+// id) in separate arrays compared field by field, with the packed tuple's
+// 32 - b priority bits as priority.  Everything but the tuple is shared, so
+// the two times isolate the packing.  Both variants compute exactly
+// mis2_run's MIS-2.
 #include "internal.h"
 
 namespace mis2 {
@@ -68,7 +69,10 @@ struct UnpackedTuples {
       const uint64_t it = p.variant == MIS2_HASH_FIXED ? 0ull : (uint64_t)iter;
       h = xorshift_star64(xorshift_star64(it) ^ xorshift_star64((uint64_t)v) ^ p.seed);
     }
-    return V{1u, (uint32_t)(h >> 32), (uint32_t)v};
+    // the 32 - b priority bits of Eq. 1's packed tuple (b = p.b): the same
+    // order as the packed form, kept in a field of its own
+    const uint32_t prio = p.b >= 32 ? 0u : (uint32_t)(h & ((1ull << (32 - p.b)) - 1ull));
+    return V{1u, prio, (uint32_t)v};
   }
   __device__ __forceinline__ static bool undecided(V x) { return x.s == 1u; }
   __device__ __forceinline__ static bool is_in(V x) { return x.s == 0u; }

@@ -1,7 +1,8 @@
 """The packed-tuple ablation (Section V-C, Fig. 2): Algorithm 1 through the
 plain tuple engine with Eq. 1's packed tuple must give mis2_run's MIS-2 (the
 oracle's, bit for bit, rounds included); with unpacked (status, priority,
-id) tuples it must give the oracle's unpacked restatement."""
+id) tuples it must give the oracle's unpacked restatement, which holds the
+same priority bits and so the same MIS-2."""
 import numpy as np
 import pytest
 
@@ -58,17 +59,20 @@ def test_unpacked_tuple_engine_matches_the_oracle(name, g, variant):
     assert rounds == ref[2]
 
 
-def test_unpacked_breaks_truncated_ties_by_priority():
+def test_packed_and_unpacked_break_priority_ties_by_id():
+    """Vertices 0 and w adjacent among 2^20 - 2 isolated ones, w drawing the
+    same 12 priority bits as vertex 0 in round 0: both tuple forms give the
+    tie to the smaller id, and the unpacked engine equals the packed one."""
     n = (1 << 20) - 2
-    g = gg.graph_from_edges(n, [(0, 1)])
-    seed = next(s for s in range(200000)
-                if (oracle.priority_tuple(0, 0, n, s) >> 20) == (oracle.priority_tuple(0, 1, n, s) >> 20)
-                and (oracle.priority_tuple(0, 0, 1, s) >> 2) > (oracle.priority_tuple(0, 1, 1, s) >> 2))
+    p0 = oracle.priority_tuple(0, 0, n, 0) >> 20
+    w = next(v for v in range(1, n) if oracle.priority_tuple(0, v, n, 0) >> 20 == p0)
+    g = gg.graph_from_edges(n, [(0, w)])
     dg = mis2.DeviceGraph.from_host(g)
-    pk = make_ctx(g, ablation=PACKED).run(dg, seed)[0].cpu().numpy()
-    up = make_ctx(g, ablation=UNPACKED).run(dg, seed)[0].cpu().numpy()
-    assert (pk[0], pk[1]) == (1, 0) and (up[0], up[1]) == (0, 1)
-    assert np.array_equal(up, oracle.mis2_unpacked(g, seed)[0])
+    pk = make_ctx(g, ablation=PACKED).run(dg, 0)[0].cpu().numpy()
+    up = make_ctx(g, ablation=UNPACKED).run(dg, 0)[0].cpu().numpy()
+    assert pk[0] == 1 and pk[w] == 0
+    assert np.array_equal(up, pk)
+    assert np.array_equal(up, oracle.mis2_unpacked(g, 0)[0])
 
 
 def test_other_calls_refuse_the_tuple_engine():
