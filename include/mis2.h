@@ -162,7 +162,8 @@ typedef struct {
   double kernel_ms[MIS2_NUM_KERNEL_CLASSES];
   int64_t kernel_launches[MIS2_NUM_KERNEL_CLASSES];
   int64_t launches;         /* CUDA kernels launched by the last call (always counted) */
-  /* device loop with timing: globaltimer ns of [0] the launch start, then per
+  /* device loop with timing: globaltimer ns of [0] block 0's start and [1]
+   * the end of its round-0 set-up, then per
    * grid barrier b (b = 0 after set-up, 2r+1 after round r's column step,
    * 2r+2 after its decide step) the last block's arrival [2+2b] and block 0's
    * departure [3+2b]; one row per MIS-2 (phase-1, phase-2) */
@@ -431,22 +432,29 @@ int mis2_server_replay(mis2_server* s, int32_t n_pool, const mis2_csr* pool_host
  * arguments, minus the context), for callers that cannot call cudaMalloc --
  * processes whose device memory is fully budgeted up front, or whose
  * allocator owns the whole device, and latency-critical code that must not
- * block on cudaMalloc / cudaFree.  The paper has no counterpart; this is a
- * deployment variant of Algorithm 1's driver.
+ * block on cudaMalloc / cudaFree.  The paper has no counterpart.
  *
  * Scratch comes from a fixed array of about 14.7 MB compiled into the
- * library, present on every GPU that loads the library until the process
- * exits.  Graphs with more than MIS2_NOALLOC_MAX_N vertices are rejected with
- * MIS2_ERR_INVALID_ARG (message in mis2_last_error()); nnz is not limited,
- * since colind stays in caller memory.  No cudaMalloc, cudaFree or other
- * allocating call is made: host-side counters use stack memory.
+ * library.  The array is committed when the library's device code is loaded
+ * into a context: with CUDA's default lazy module loading that is usually
+ * the first call of this function on a device, so a process that budgets
+ * device memory up front must make one (small) warm-up call before its
+ * allocator reserves the rest of the device; the array then stays committed
+ * until the context ends.  Graphs with more than MIS2_NOALLOC_MAX_N vertices
+ * are rejected with MIS2_ERR_INVALID_ARG (message in mis2_last_error());
+ * nnz is not limited, since colind stays in caller memory.  The call itself
+ * makes no cudaMalloc, cudaFree or other allocating call: host-side counters
+ * use stack memory.
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any CUDA
- * stream capture.  All calls share the array, so calls that overlap on the
- * GPU (concurrent streams or threads) race and give wrong results; serialise
- * them.  The round loop runs on the device (MIS2_LOOP_DEVICE) with the
- * default configuration.  Synchronises `stream`.
+ * The array's device address is looked up (cudaGetSymbolAddress) the first
+ * time a context calls this function -- once per device, or again after
+ * cudaDeviceReset or when the caller made another context current; make that
+ * first call before any CUDA stream capture.  All calls share the array and
+ * it keeps the last call's contents (the counters are cleared at the start of
+ * each call), so calls that overlap on the GPU (concurrent streams or
+ * threads) race and give wrong results; serialise them.  The round loop runs
+ * on the device (MIS2_LOOP_DEVICE) with the default configuration.
+ * Synchronises `stream`.
  */
 #define MIS2_NOALLOC_MAX_N 262144
 int mis2_run_noalloc(const mis2_csr* g, uint64_t seed, uint8_t* in_set, int32_t* roots,

@@ -62,6 +62,30 @@ int timer_collect(mis2_ctx* c) {
   return MIS2_OK;
 }
 
+int resident_blocks_per_sm(const mis2_ctx* c, const void* kernel, int block, int* per_sm, int smem) {
+  struct Entry {
+    const void* kernel;
+    int device, block, smem, per_sm;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> known;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& e : known)
+      if (e.kernel == kernel && e.device == c->device && e.block == block && e.smem == smem) {
+        *per_sm = e.per_sm;
+        return MIS2_OK;
+      }
+  }
+  if (smem > 48 * 1024) MIS2_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int n = 0;
+  MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem));
+  std::lock_guard<std::mutex> lk(mu);
+  known.push_back(Entry{kernel, c->device, block, smem, n});
+  *per_sm = n;
+  return MIS2_OK;
+}
+
 PrioCfg make_prio(const mis2_ctx* c, int64_t n, uint64_t seed) {
   PrioCfg p;
   p.seed = seed;

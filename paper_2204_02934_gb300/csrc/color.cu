@@ -343,7 +343,7 @@ int color_rounds_t(mis2_ctx* c, const GraphView<I>& gv, const GraphArgs& ga, con
     // every round in one cooperative launch (all blocks resident)
     auto kern = pack ? k_color_loop<G, true, I> : k_color_loop<G, false, I>;
     int per_sm = 0;
-    MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+    MIS2_TRY(resident_blocks_per_sm(c, (const void*)kern, kBlock, &per_sm));
     if (per_sm < 1) return MIS2_ERR_CUDA;
     const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 6;
     const int blocks = c->sm_count * std::min(per_sm, want);

@@ -52,14 +52,17 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
 
-  mis_init_rows<I>(g, a.labels, p, a.T, a.M, a.wl1[0], a.wl2[0], ctr + ctr_c1(0, 0), ctr + ctr_c2(0, 0),
-                   a.warp_degree, a.block_degree);
   int64_t* ts = a.ts;
-  if (ts != nullptr && tid == 0) ts[0] = global_ns();  // start of the launch
+  if (ts != nullptr && tid == 0) ts[0] = global_ns();  // block 0 starts
+  // worklist 2 starts equal to worklist 1: round 0's column step reads the
+  // worklist-1 lists, so only worklist 2's sizes are set here
+  const RowLists none{{nullptr, nullptr, nullptr}};
+  mis_init_rows<I>(g, a.labels, p, a.T, a.M, a.wl1[0], none, ctr + ctr_c1(0, 0), ctr + ctr_c2(0, 0),
+                   a.warp_degree, a.block_degree);
+  if (ts != nullptr && tid == 0) ts[1] = global_ns();  // block 0 has set up its vertices
   if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr, a.barrier_extra)) return;
 
   constexpr bool nowl = NOWL;
-  const RowLists none{{nullptr, nullptr, nullptr}};
   int r = 0;
   for (;; r++) {
     const int slot = r % 3, nslot = (r + 1) % 3, zslot = (r + 2) % 3;
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     const bool tr_on = a.dtr != nullptr && r < MIS2_TRACE_CAP;
     int64_t* d2 = tr_on ? a.dtr + r * 4 + 3 : nullptr;
     int64_t* d1 = tr_on ? a.dtr + r * 4 + 2 : nullptr;
-    const RowLists in2 = nowl ? a.wl2[0] : a.wl2[r & 1], out2 = nowl ? none : a.wl2[(r + 1) & 1];
+    const RowLists in2 = (nowl || r == 0) ? a.wl1[0] : a.wl2[r & 1], out2 = nowl ? none : a.wl2[(r + 1) & 1];
     const RowLists in1 = nowl ? a.wl1[0] : a.wl1[r & 1], out1 = nowl ? none : a.wl1[(r + 1) & 1];
     // ---- column step
     if (tid < kClasses) ctr[ctr_c1(nslot, (int)tid)] = 0;
@@ -141,7 +144,7 @@ template <int G, typename I>
 static int launch_loop(mis2_ctx* c, GraphView<I> gv, PrioCfg p, LoopArgs la, cudaStream_t st) {
   auto kern = la.no_worklists ? k_mis_loop<G, I, true> : k_mis_loop<G, I, false>;
   int per_sm = 0;
-  MIS2_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+  MIS2_TRY(resident_blocks_per_sm(c, (const void*)kern, kBlock, &per_sm));
   if (per_sm < 1) return MIS2_ERR_CUDA;
   const int want = c->cfg.loop_blocks_per_sm > 0 ? c->cfg.loop_blocks_per_sm : 2;
   const int blocks = c->sm_count * std::min(per_sm, want);

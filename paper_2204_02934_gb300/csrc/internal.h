@@ -190,6 +190,13 @@ int timer_collect(mis2_ctx* c);
 int pick_group_lanes(const mis2_ctx* c, const GraphArgs& g);
 int pick_warp_degree(const mis2_ctx* c, const GraphArgs& g);
 int grid_for(const mis2_ctx* c, int64_t items, int items_per_block, int blocks_per_sm = 8);
+// Resident blocks per SM of a kernel at `block` threads and `smem` bytes of
+// dynamic shared memory on the context's device
+// (cudaOccupancyMaxActiveBlocksPerMultiprocessor), asked once per (kernel,
+// device, block, smem) and remembered, so a persistent launch pays no
+// host-side query.  Raises the kernel's dynamic shared memory limit to
+// `smem` first when it exceeds the default 48 KB.
+int resident_blocks_per_sm(const mis2_ctx* c, const void* kernel, int block, int* per_sm, int smem = 0);
 
 // MIS-2 of g (labels == null) or of {v : labels[v] == -1}; leaves T with
 // IN/OUT.  trace_phase 0/1 selects the trace slot.  Host-driven loop.

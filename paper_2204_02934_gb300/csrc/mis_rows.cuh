@@ -473,80 +473,91 @@ __device__ __forceinline__ void decide_block_rows(const GraphView<I>& g, uint32_
 }
 
 // Round-0 set-up: T_v for every vertex of the (sub)graph, OUT / M = 0 for
-// the others, and both worklists filled per row class (Algorithm 1:
-// worklist1 = worklist2 = all vertices).  labels == null: whole graph;
-// otherwise the subgraph {v : labels[v] == -1}.
+// the others, and worklist 1 filled per row class (Algorithm 1: worklist1 =
+// worklist2 = all vertices; worklist 2 is written too when wl2.l[0] is not
+// null, else only its sizes, since its round-0 content equals worklist 1's).
+// labels == null: whole graph; otherwise the subgraph {v : labels[v] == -1}.
 // Each block takes a contiguous vertex range and appends its members of a
 // class as one ascending run (one reservation per block and class), so the
 // lists start as long ascending runs: the passes stage 32 consecutive rows
-// as one span, and keep that order in their outputs.  Every thread of the
-// block must call this.
+// as one span, and keep that order in their outputs.  Within the block each
+// thread owns a contiguous sub-range, so one block scan of the per-thread
+// class counts places every entry; the row bounds of a thread's vertices are
+// loaded kInitBatch at a time, so their latencies overlap.  Every thread of
+// the block must call this.
+constexpr int kInitBatch = 16;
+
 template <typename I>
 __device__ __forceinline__ void mis_init_rows(const GraphView<I>& g, const int32_t* labels, const PrioCfg& p,
                                               uint32_t* T, uint32_t* M, RowLists wl1, RowLists wl2,
                                               int32_t* c1, int32_t* c2, int32_t warp_degree,
                                               int32_t block_degree) {
   __shared__ int sh_scan[40];
-  __shared__ int sh_cnt[kClasses];
   __shared__ int32_t sh_base1[kClasses], sh_base2[kClasses];
   const int64_t per = (g.n + gridDim.x - 1) / gridDim.x;
   const int64_t v0 = min(g.n, (int64_t)blockIdx.x * per), v1 = min(g.n, v0 + per);
-  if (threadIdx.x < kClasses) sh_cnt[threadIdx.x] = 0;
-  __syncthreads();
-  auto class_of = [&](int64_t v) {
-    if (labels != nullptr && ld<false>(labels + v) != -1) return -1;
-    int64_t s, e;
-    row_range(g, v, s, e);
-    return row_class(e - s, warp_degree, block_degree);
+  const int64_t q = (v1 - v0 + blockDim.x - 1) / blockDim.x;
+  const int64_t t0 = min(v1, v0 + (int64_t)threadIdx.x * q), t1 = min(v1, t0 + q);
+  // class of each vertex of [b, b + kInitBatch) ∩ [t0, t1) (-1: outside the
+  // (sub)graph or the range), from the kInitBatch + 1 consecutive row
+  // offsets rowptr[b ..], all loaded before any is used
+  auto classes = [&](int64_t b, int (&cls)[kInitBatch]) {
+    I rp[kInitBatch + 1];
+    int32_t lab[kInitBatch];
+#pragma unroll
+    for (int k = 0; k <= kInitBatch; k++) rp[k] = b + k <= t1 ? __ldg(g.rowptr + b + k) : (I)0;
+#pragma unroll
+    for (int k = 0; k < kInitBatch; k++) lab[k] = (labels != nullptr && b + k < t1) ? ld<false>(labels + b + k) : -1;
+#pragma unroll
+    for (int k = 0; k < kInitBatch; k++)
+      cls[k] = (b + k < t1 && lab[k] == -1) ? row_class((int64_t)(rp[k + 1] - rp[k]), warp_degree, block_degree) : -1;
   };
-  int cnt0 = 0, cnt_hi = 0;  // class 0; classes 1 and 2 in 16-bit halves (per thread: < 2^16 vertices)
-  for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-    const int cls = class_of(v);
-    if (cls >= 0) {
-      T[v] = make_tuple(p, 0u, (uint32_t)v);
-      cnt0 += cls == 0;
-      cnt_hi += cls == 1 ? 1 : (cls == 2 ? 1 << 16 : 0);
-    } else {
-      T[v] = kOut;
-      M[v] = 0u;
+  int cnt[kClasses] = {0, 0, 0};
+  for (int64_t b = t0; b < t1; b += kInitBatch) {
+    int cls[kInitBatch];
+    classes(b, cls);
+#pragma unroll
+    for (int k = 0; k < kInitBatch; k++) {
+      const int64_t v = b + k;
+      if (v >= t1) break;
+      if (cls[k] >= 0) {
+        T[v] = make_tuple(p, 0u, (uint32_t)v);
+        cnt[0] += cls[k] == 0;
+        cnt[1] += cls[k] == 1;
+        cnt[2] += cls[k] == 2;
+      } else {
+        T[v] = kOut;
+        M[v] = 0u;
+      }
     }
   }
-  {
-    const int x0 = __reduce_add_sync(kFull, (unsigned)cnt0);
-    const int x1 = __reduce_add_sync(kFull, (unsigned)(cnt_hi & 0xFFFF));
-    const int x2 = __reduce_add_sync(kFull, (unsigned)(cnt_hi >> 16));
-    if (lane_id() == 0) {
-      if (x0 > 0) atomicAdd(sh_cnt + 0, x0);
-      if (x1 > 0) atomicAdd(sh_cnt + 1, x1);
-      if (x2 > 0) atomicAdd(sh_cnt + 2, x2);
+  int pos[kClasses];
+#pragma unroll
+  for (int k = 0; k < kClasses; k++) {
+    int total;
+    pos[k] = block_exclusive_scan(cnt[k], sh_scan, &total);
+    if (threadIdx.x == 0) {
+      sh_base1[k] = total > 0 ? atomicAdd(c1 + k, total) : 0;
+      sh_base2[k] = total > 0 ? atomicAdd(c2 + k, total) : 0;
     }
   }
   __syncthreads();
-  if (threadIdx.x < kClasses) {
-    const int x = sh_cnt[threadIdx.x];
-    sh_base1[threadIdx.x] = x > 0 ? atomicAdd(c1 + threadIdx.x, x) : 0;
-    sh_base2[threadIdx.x] = x > 0 ? atomicAdd(c2 + threadIdx.x, x) : 0;
-  }
-  __syncthreads();
-  int run0 = 0, run1 = 0, run2 = 0;
-  for (int64_t t0 = v0; t0 < v1; t0 += blockDim.x) {
-    const int64_t v = t0 + threadIdx.x;
-    const int cls = v < v1 ? class_of(v) : -1;
-    // the three class counts of the tile packed in 10-bit fields
-    const int packed = cls < 0 ? 0 : 1 << (10 * cls);
-    int tile_total;
-    const int x = block_exclusive_scan(packed, sh_scan, &tile_total);
-    if (cls >= 0) {
-      const int run = cls == 0 ? run0 : (cls == 1 ? run1 : run2);
-      const int pos = run + ((x >> (10 * cls)) & 1023);
-      int32_t* l1 = cls == 0 ? wl1.l[0] : (cls == 1 ? wl1.l[1] : wl1.l[2]);
-      int32_t* l2 = cls == 0 ? wl2.l[0] : (cls == 1 ? wl2.l[1] : wl2.l[2]);
-      l1[sh_base1[cls] + pos] = (int32_t)v;
-      l2[sh_base2[cls] + pos] = (int32_t)v;
+  const bool both = wl2.l[0] != nullptr;
+  for (int64_t b = t0; b < t1; b += kInitBatch) {
+    int cls[kInitBatch];
+    classes(b, cls);
+#pragma unroll
+    for (int k = 0; k < kInitBatch; k++) {
+      const int c = cls[k];
+      if (c < 0) continue;
+      const int at = c == 0 ? pos[0]++ : (c == 1 ? pos[1]++ : pos[2]++);
+      int32_t* L1 = c == 0 ? wl1.l[0] : (c == 1 ? wl1.l[1] : wl1.l[2]);
+      L1[sh_base1[c] + at] = (int32_t)(b + k);
+      if (both) {
+        int32_t* L2 = c == 0 ? wl2.l[0] : (c == 1 ? wl2.l[1] : wl2.l[2]);
+        L2[sh_base2[c] + at] = (int32_t)(b + k);
+      }
     }
-    run0 += tile_total & 1023;
-    run1 += (tile_total >> 10) & 1023;
-    run2 += (tile_total >> 20) & 1023;
   }
 }
 

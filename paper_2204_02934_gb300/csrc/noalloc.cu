@@ -12,6 +12,8 @@
 // process exits.  All calls share it and it keeps the last call's contents:
 // the counters are cleared at the start of each call, and calls that overlap
 // on the GPU (two streams, two host threads) race on it.
+#include <cuda.h>  // CUcontext / CUresult types only (see context_id below)
+
 #include <cstring>
 #include <mutex>
 
@@ -32,22 +34,79 @@ constexpr int64_t kNoAllocBytes = kOffTile + 4 * kNoAllocTiles;
 
 static __device__ __align__(256) unsigned char g_mis2_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
-static std::mutex g_noalloc_mu;
-static unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// The array's device address belongs to the CUDA context that loaded the
+// library's module: a device's primary context normally lives until the
+// process exits, but cudaDeviceReset (or a caller that switches to a context
+// of its own) brings a new one, where the array can sit elsewhere.  The
+// address is therefore looked up once per context and cached under the
+// context's unique id (cuCtxGetId; ids are never reused within a process).
+// The two driver calls are reached through the runtime's entry-point lookup,
+// so the library still links no driver library.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, never a device address).
-static int noalloc_scratch(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return MIS2_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (g_noalloc_addr[dev] == nullptr) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_mis2_noalloc_scratch);
-    if (e != cudaSuccess) return set_cuda_error(e);
-    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+struct ScratchSlot {
+  unsigned long long ctx_id;
+  unsigned char* addr;
+};
+constexpr int kNoAllocSlots = 64;
+static std::mutex g_noalloc_mu;
+static ScratchSlot g_noalloc_slots[kNoAllocSlots] = {};
+static int g_noalloc_next = 0;
+static CtxGetCurrentFn g_ctx_get_current = nullptr;
+static CtxGetIdFn g_ctx_get_id = nullptr;
+
+static int driver_entry(const char* name, void** fn) {
+  cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+  const cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  if (q != cudaDriverEntryPointSuccess || *fn == nullptr) {
+    set_error_text("mis2_run_noalloc: driver entry point not found");
+    return MIS2_ERR_CUDA;
   }
-  *out = g_noalloc_addr[dev];
+  return MIS2_OK;
+}
+
+// Unique id of the calling thread's current context (the runtime's primary
+// context of the current device unless the caller made another current).
+// Called with g_noalloc_mu held.
+static int context_id(unsigned long long* id) {
+  if (g_ctx_get_current == nullptr) {
+    MIS2_TRY(driver_entry("cuCtxGetCurrent", reinterpret_cast<void**>(&g_ctx_get_current)));
+    MIS2_TRY(driver_entry("cuCtxGetId", reinterpret_cast<void**>(&g_ctx_get_id)));
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return MIS2_ERR_CUDA;
+  if (ctx == nullptr) {
+    // no context current yet in this thread: a runtime call that needs the
+    // device binds the current device's primary context
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_mis2_noalloc_scratch);
+    if (e != cudaSuccess) return set_cuda_error(e);
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return MIS2_ERR_CUDA;
+  }
+  if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return MIS2_ERR_CUDA;
+  return MIS2_OK;
+}
+
+// Device address of the scratch array in the current context (the
+// host-side symbol is only a stand-in, never a device address): looked up
+// with cudaGetSymbolAddress once per context, with that context current.
+static int noalloc_scratch(unsigned char** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  unsigned long long id = 0;
+  MIS2_TRY(context_id(&id));
+  for (const ScratchSlot& sl : g_noalloc_slots)
+    if (sl.addr != nullptr && sl.ctx_id == id) {
+      *out = sl.addr;
+      return MIS2_OK;
+    }
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_mis2_noalloc_scratch);
+  if (e != cudaSuccess) return set_cuda_error(e);
+  g_noalloc_slots[g_noalloc_next] = ScratchSlot{id, static_cast<unsigned char*>(p)};
+  g_noalloc_next = (g_noalloc_next + 1) % kNoAllocSlots;
+  *out = static_cast<unsigned char*>(p);
   return MIS2_OK;
 }
 
@@ -66,7 +125,7 @@ extern "C" int mis2_run_noalloc(const mis2_csr* g, uint64_t seed, uint8_t* in_se
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_cuda_error(e);
   unsigned char* base = nullptr;
-  MIS2_TRY(noalloc_scratch(dev, &base));
+  MIS2_TRY(noalloc_scratch(&base));
 
   // A context on the stack whose scratch pointers all point into the array.
   mis2_ctx c;

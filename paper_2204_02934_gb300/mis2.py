@@ -20,7 +20,7 @@ from . import _build
 MIS2_OK = 0
 STATUS = {
     0: "MIS2_OK", -1: "MIS2_ERR_INVALID_ARG", -2: "MIS2_ERR_OUT_OF_MEMORY", -3: "MIS2_ERR_CUDA",
-    -4: "MIS2_ERR_BAD_GRAPH", -5: "MIS2_ERR_TIMEOUT", -6: "MIS2_ERR_NO_PROGRESS",
+    -4: "MIS2_ERR_BAD_GRAPH", -5: "MIS2_ERR_TIMEOUT", -6: "MIS2_ERR_NO_PROGRESS", -7: "MIS2_ERR_CANCELLED",
 }
 MIS2_AGG_ALG3, MIS2_AGG_BASIC = 0, 1
 MIS2_HASH_XORSHIFT_STAR, MIS2_HASH_XORSHIFT, MIS2_HASH_FIXED = 0, 1, 2

@@ -72,6 +72,7 @@ def test_every_status_code_has_a_name():
     assert "MIS2_ERR_CANCELLED" in codes and len(codes) >= 8
     for name, val in codes.items():
         assert mis2.mis2_status_string(val) == name
+        assert mis2.STATUS[val] == name  # the binding's error text names it too
     assert mis2.mis2_status_string(-99) == "MIS2_ERR_UNKNOWN"
 
 
