@@ -194,6 +194,7 @@ static int alloc_scratch(mis2_ctx* c) {
   MIS2_TRY(dev_alloc(c, &s.tmp, nnz + 4));
   MIS2_TRY(dev_alloc(c, &s.labels_tmp, n));
   MIS2_TRY(dev_alloc(c, &s.radix, group_scratch_words(n)));
+  MIS2_TRY(dev_alloc(c, &s.cand, 3 * n));
   MIS2_TRY(dev_alloc(c, &s.bitmaps, (int64_t)coarse_bitmap_blocks(c) * ((n + 31) / 32)));
   MIS2_TRY(dev_alloc(c, &s.chunk_off, n + 1));
   const int64_t giant_cap = nnz / kGiantRow + 1;

@@ -102,7 +102,11 @@ struct GiantList {
   int32_t cur_slot;
 };
 
-template <typename I, typename FB>
+// CONVERGED: every lane calls fb for every batch of 32 members, with one
+// 32-entry array (lanes without a staged row get all -1), so fb may use
+// warp-wide primitives; otherwise only lanes with a staged row call it, with
+// the narrowest of 8, 16 or 32 entries that bounds the batch's rows.
+template <typename I, bool CONVERGED = false, typename FB>
 __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int32_t* labels, const int32_t* members,
                                                int64_t mb, int64_t me, int32_t a, int32_t* stage_warp, FB&& fb,
                                                const GiantList* giant = nullptr) {
@@ -115,7 +119,9 @@ __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int3
     const int len = has && e - s <= kLaneRowMax ? (int)(e - s) : -1;
     int wd;
     const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, stage_warp, &wd);
-    if (len > 0) {
+    if constexpr (CONVERGED) {
+      staged_labels<32>(labels, mine, len, a, fb);
+    } else if (len > 0) {
       if (wd == 8) staged_labels<8>(labels, mine, len, a, fb);
       else if (wd == 16) staged_labels<16>(labels, mine, len, a, fb);
       else staged_labels<32>(labels, mine, len, a, fb);
@@ -140,9 +146,12 @@ __device__ __forceinline__ void walk_aggregate(const GraphView<I>& g, const int3
       const int j = __ffs(longm) - 1;
       longm &= longm - 1;
       const int64_t sj = __shfl_sync(kFull, s, j), ej = __shfl_sync(kFull, e, j);
-      for (int64_t p = (sj & ~int64_t(3)) + 4 * lane; p < ej; p += 128) {
+      // warp-uniform trip count (every lane calls fb the same number of
+      // times); lanes past the row's end see only -1 labels
+      for (int64_t pb = sj & ~int64_t(3); pb < ej; pb += 128) {
+        const int64_t p = pb + 4 * lane;
         int32_t w4[4];
-        if (g.vec && p + 4 <= g.nnz) {
+        if (p < ej && g.vec && p + 4 <= g.nnz) {
           const int4 q = __ldg(reinterpret_cast<const int4*>(g.colind + p));
           w4[0] = q.x, w4[1] = q.y, w4[2] = q.z, w4[3] = q.w;
         } else {
@@ -340,6 +349,187 @@ __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const i
   }
 }
 
+// Aggregates of mesh-like graphs (tens of members, each row touching a
+// handful of other aggregates) in two steps.  k_coarse_cand: for every
+// vertex in index order (a lane per vertex, 32 consecutive rows staged by the
+// warp), the labels among its neighbours other than its own, at most
+// kCand of them (-1 = unused slot), each label written unless it equals one
+// of the last four written (a row meets its few neighbour aggregates in
+// runs, so the list stays short; a repeat that slips through is harmless,
+// the merge removes it).  A vertex needing more slots, or with a row longer
+// than 32 entries, gets slot 0 = -2.
+constexpr int kCand = 12;  // candidate slots per vertex: three int4
+
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_coarse_cand(GraphView<I> g, const int32_t* labels, int4* cand) {
+  __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
+  __shared__ int32_t outs[kBlock / 32][32 * (kCand + 1)];
+  const int lane = lane_id();
+  int32_t* area = stage[threadIdx.x >> 5];
+  int32_t* my = outs[threadIdx.x >> 5] + lane * (kCand + 1);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < g.n; base += nw * 32) {
+    const int64_t v = base + lane;
+    const bool has = v < g.n;
+    int64_t s = 0, e = 0;
+    int32_t a = -1;
+    if (has) {
+      row_range(g, v, s, e);
+      a = labels[v];
+    }
+    const int len = has && e - s <= kLaneRowMax ? (int)(e - s) : -1;
+    const int32_t* mine = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, area);
+    int32_t lab[kLaneRowMax];
+#pragma unroll
+    for (int k = 0; k < kLaneRowMax; k++) lab[k] = k < len ? labels[mine[k]] : a;
+    int32_t w0 = -1, w1 = -1, w2 = -1, w3 = -1;  // the last four labels written
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < kLaneRowMax; k++) {
+      const int32_t l = lab[k];
+      if (l != a && l != w0 && l != w1 && l != w2 && l != w3) {
+        if (cnt < kCand) my[cnt] = l;
+        cnt++;
+        w3 = w2;
+        w2 = w1;
+        w1 = w0;
+        w0 = l;
+      }
+    }
+    if (has) {
+      int32_t o[kCand];
+#pragma unroll
+      for (int k = 0; k < kCand; k++) o[k] = k < cnt ? my[k] : -1;
+      if (cnt > kCand || len < 0) o[0] = -2;
+#pragma unroll
+      for (int q = 0; q < kCand / 4; q++)
+        cand[(kCand / 4) * v + q] = make_int4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+    }
+    __syncwarp();  // the staged rows are rewritten by the next batch
+  }
+}
+
+// k_coarse_merge: a warp per aggregate, a member per lane (two passes for up
+// to 64 members).  The members' labels from k_coarse_cand go into a
+// shared-memory hash set, one insertion per distinct label per step (lanes
+// holding equal labels are matched first); the set, at most 32 labels, is
+// then sorted across the lanes and written in ascending order.  Aggregates
+// with more members, a member flagged by k_coarse_cand or more than 32
+// distinct labels go to `rest` (the general hash-set kernel); small
+// aggregates are k_coarse_small's.
+constexpr int kMergeSlots = 128;
+constexpr int kMergeMembers = 64;
+
+__global__ void __launch_bounds__(kBlock) k_coarse_merge(int64_t n_aggs, const int32_t* agg_ptr,
+                                                         const int32_t* members, const int32_t* ub,
+                                                         const int32_t* ub_ptr, const int4* cand, int32_t* tmp,
+                                                         int32_t* c_cnt, int32_t* rest, int32_t* rest_cnt,
+                                                         bool small_on) {
+  __shared__ int32_t tabs[kBlock / 32][kMergeSlots];
+  __shared__ int32_t dcnt[kBlock / 32];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  int32_t* tab = tabs[wib];
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
+    const int32_t p0 = agg_ptr[a], M = agg_ptr[a + 1] - p0;
+    const int32_t ua = ub[a];
+    if (small_aggregate(M, ua, small_on)) continue;  // k_coarse_small's
+    if (ua == 0) {  // no fine entries: an empty row
+      if (lane == 0) c_cnt[a] = 0;
+      continue;
+    }
+    if (M > kMergeMembers) {
+      if (lane == 0) rest[atomicAdd(rest_cnt, 1)] = (int32_t)a;
+      continue;
+    }
+#pragma unroll
+    for (int j = lane; j < kMergeSlots; j += 32) tab[j] = -1;
+    if (lane == 0) dcnt[wib] = 0;
+    __syncwarp();
+    bool bad = false;
+    for (int m0 = 0; m0 < M; m0 += 32) {  // warp-uniform
+      int32_t cs[kCand];
+#pragma unroll
+      for (int t = 0; t < kCand; t++) cs[t] = -1;
+      if (m0 + lane < M) {
+        const int64_t u = members[p0 + m0 + lane];
+#pragma unroll
+        for (int q = 0; q < kCand / 4; q++) {
+          const int4 c = cand[(kCand / 4) * u + q];
+          cs[4 * q] = c.x;
+          cs[4 * q + 1] = c.y;
+          cs[4 * q + 2] = c.z;
+          cs[4 * q + 3] = c.w;
+        }
+      }
+      bad |= cs[0] == -2;
+      // as many steps as the longest list of the warp (lists fill from slot 0)
+      int mine = 0;
+#pragma unroll
+      for (int t = 0; t < kCand; t++) mine += cs[t] >= 0 ? 1 : 0;
+      const int steps = (int)__reduce_max_sync(kFull, (unsigned)mine);
+#pragma unroll
+      for (int t = 0; t < kCand; t++) {
+        if (t >= steps) break;  // warp-uniform
+        const int32_t l = cs[t] >= 0 ? cs[t] : -1;
+        const unsigned peers = __match_any_sync(kFull, l);
+        if (l >= 0 && lane == __ffs(peers) - 1) {
+          uint32_t h = ((uint32_t)l * 2654435761u) >> 25;
+          for (int probe = 0; probe < kMergeSlots; probe++) {
+            const int32_t old = atomicCAS(tab + h, -1, l);
+            if (old == -1) {
+              atomicAdd(dcnt + wib, 1);
+              break;
+            }
+            if (old == l) break;
+            h = (h + 1) & (kMergeSlots - 1);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    const int nd = dcnt[wib];
+    if (__any_sync(kFull, bad) || nd > 32) {
+      if (lane == 0) rest[atomicAdd(rest_cnt, 1)] = (int32_t)a;
+      __syncwarp();
+      continue;
+    }
+    // the set's labels, one per lane, then a bitonic sort across the lanes
+    int32_t v[kMergeSlots / 32];
+    int nv = 0;
+#pragma unroll
+    for (int r = 0; r < kMergeSlots / 32; r++) {
+      v[r] = tab[lane * (kMergeSlots / 32) + r];
+      nv += v[r] >= 0 ? 1 : 0;
+    }
+    int pos = nv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, pos, o);
+      if (lane >= o) pos += y;
+    }
+    pos -= nv;
+    __syncwarp();  // every lane has read its slots
+#pragma unroll
+    for (int r = 0; r < kMergeSlots / 32; r++)
+      if (v[r] >= 0) tab[pos++] = v[r];
+    __syncwarp();
+    int32_t x = lane < nd ? tab[lane] : 0x7FFFFFFF;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const int32_t o = __shfl_xor_sync(kFull, x, stride);
+        const bool up = (lane & size) == 0, lower = (lane & stride) == 0;
+        x = (lower == up) ? min(x, o) : max(x, o);
+      }
+    }
+    if (lane < nd) tmp[ub_ptr[a] + lane] = x;
+    if (lane == 0) c_cnt[a] = nd;
+    __syncwarp();
+  }
+}
+
 // Warp per aggregate: insert every neighbour label into a shared-memory hash
 // set (256 slots, linear probing); first insertions form the distinct list,
 // which is then sorted (bitonic, a few dozen entries) and written out.  An
@@ -351,11 +541,13 @@ static_assert(kHashSlots + 256 <= kSortCap, "hash table and distinct list share 
 
 __device__ __forceinline__ uint32_t label_hash(int32_t l) { return ((uint32_t)l * 2654435761u) >> 24; }
 
+// With `list` (the aggregates k_coarse_merge left over, *list_cnt of them)
+// only those; otherwise every aggregate that is not k_coarse_small's.
 template <typename I>
 __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
     GraphView<I> g, const int32_t* labels, int64_t n_aggs, const int32_t* agg_ptr, const int32_t* members,
     const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt, int32_t* large, int32_t* large_cnt,
-    bool small_on) {
+    bool small_on, const int32_t* list, const int32_t* list_cnt) {
   __shared__ int32_t sbuf[kCoarseWarps][kSortCap];
   __shared__ __align__(16) int32_t stage[kCoarseWarps][kStageWarpWords];
   __shared__ int32_t scnt[kCoarseWarps];
@@ -363,9 +555,11 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
   int32_t* tab = sbuf[wib];
   int32_t* dl = sbuf[wib] + kHashSlots;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < n_aggs; a += nw) {
+  const int64_t items = list != nullptr ? (int64_t)block_load(list_cnt) : n_aggs;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < items; i += nw) {
+    const int64_t a = list != nullptr ? (int64_t)list[i] : i;
     const int32_t ua = ub[a];
-    if (small_aggregate(agg_ptr[a + 1] - agg_ptr[a], ua, small_on)) continue;  // k_coarse_small's
+    if (list == nullptr && small_aggregate(agg_ptr[a + 1] - agg_ptr[a], ua, small_on)) continue;  // k_coarse_small's
     if (ua > kWarpEntries) {
       if (lane == 0) large[atomicAdd(large_cnt, 1)] = (int32_t)a;
       continue;
@@ -375,16 +569,21 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
     __syncwarp();
     const int64_t mb = agg_ptr[a], me = agg_ptr[a + 1];
     bool full = false;
-    walk_aggregate<I>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](auto& lab) {
+    walk_aggregate<I, true>(g, labels, members, mb, me, (int32_t)a, stage[wib], [&](auto& lab) {
       int32_t prev = -1;
 #pragma unroll
       for (int j = 0; j < (int)(sizeof(lab) / sizeof(lab[0])); j++) {
-        const int32_t l = lab[j];
+        int32_t l = lab[j];
         // past the distinct cap the aggregate goes to the bitmap path: a lane
         // stops inserting once its own insertion found the cap reached, so
         // the table holds at most kDistinctCap + 32 labels and probing ends
-        if (l < 0 || l == prev || full) continue;
-        prev = l;
+        if (l == prev || full) l = -1;
+        else if (l >= 0) prev = l;
+        // one insertion per distinct label among the lanes (lanes walking
+        // neighbouring members mostly meet the same labels at once, and
+        // compare-and-swaps on one slot serialise)
+        const unsigned peers = __match_any_sync(kFull, l);
+        if (l < 0 || lane != __ffs(peers) - 1) continue;
         uint32_t h = label_hash(l);
         for (int probe = 0; probe < kHashSlots; probe++) {
           const int32_t old = atomicCAS(tab + h, -1, l);
@@ -704,6 +903,36 @@ static GraphView<I> gview_of(const GraphArgs& g) {
   return gv;
 }
 
+// The rows of the aggregates that are neither small nor large.  Without the
+// small-aggregate kernel (aggregates of many entries, as in 3D meshes):
+// neighbour labels per vertex (k_coarse_cand), then a warp per aggregate
+// (k_coarse_merge), and the hash-set kernel for the aggregates it leaves
+// over; otherwise the hash-set kernel for every non-small aggregate.  Counts
+// its launches.
+template <typename I>
+static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t* labels, int64_t n_aggs,
+                              bool small_on, cudaStream_t st) {
+  Scratch& s = c->s;
+  const int rows_blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
+  if (small_on) {
+    k_coarse_rows<I><<<rows_blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub,
+                                                                s.ub_ptr, s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge,
+                                                                small_on, nullptr, nullptr);
+    c->launches++;
+    return MIS2_OK;
+  }
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
+  k_coarse_cand<I><<<grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
+  k_coarse_merge<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+                                                                          s.cand, s.tmp, s.c_cnt, s.left_mid,
+                                                                          s.ctr + kCtrCoarseRest, small_on);
+  k_coarse_rows<I><<<rows_blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+                                                              s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on,
+                                                              s.left_mid, s.ctr + kCtrCoarseRest);
+  c->launches += 3;
+  return MIS2_OK;
+}
+
 // Bitmaps per batch of large aggregates: as many as fit the bitmap scratch
 // (sized for the context's largest graph), at most n_aggs.
 static int32_t bitmap_slots(const mis2_ctx* c, int64_t n_aggs) {
@@ -799,10 +1028,8 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
         gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
     c->launches++;
   }
-  const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
-  k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
-                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on);
-  c->launches += 2;
+  MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st));
+  c->launches++;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   // large aggregates, in batches of `slots` bitmaps
@@ -855,9 +1082,7 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
         gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
     c->launches++;
   }
-  const int blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
-  k_coarse_rows<I><<<blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
-                                                         s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on);
+  MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st));
   const int64_t words = (n_aggs + 31) / 32;
   const int32_t slots = bitmap_slots(c, n_aggs);
   k_large_chunks<<<1, kBlock, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
@@ -871,7 +1096,7 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
                                                     s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
   k_large_emit<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, 0, slots, s.ub_ptr, s.bitmaps, words, s.tmp, s.c_cnt,
                                                    s.ctr + kCtrLargeKb);
-  c->launches += 8;
+  c->launches += 7;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));

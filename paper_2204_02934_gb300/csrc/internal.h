@@ -48,6 +48,7 @@ enum : int {
   kCtrCheckSums = 36,  // debug checks: two 64-bit entry-hash sums (words 36-39)
   kCtrInitSizes = 40,  // no-worklist mode of the host loop: round-0 list sizes (words 40-45)
   kCtrColorLeft = 48,  // colouring: uncoloured count after each round of a batch (words 48-55)
+  kCtrCoarseRest = 56,  // coarse graph: aggregates left to the hash-set kernel
   kCtrWords = 64
 };
 constexpr int kReadbackWords = 40;
@@ -112,6 +113,7 @@ struct Scratch {
   int64_t* giant_off = nullptr;   //   and their piece offsets (capacity nnz / kGiantRow + 1)
   int32_t* labels_tmp = nullptr; // labels when the caller passes none
   int32_t* radix = nullptr;       // stable grouping: per-tile digit counts (group_scratch_words)
+  int4* cand = nullptr;           // coarse graph: up to twelve neighbour labels per vertex (3n)
 };
 
 struct HostStage {  // device copies for the host-buffer entry point
