@@ -367,37 +367,53 @@ def run_batch_compare(steps=3, warmup=2, n_graphs=512, seed=7, min_n=1000):
     """Batched hierarchies vs per-graph plain launches on the mixed-size batch
     (2D 5-pt / 3D 7-pt / 2D RGG, 1k-200k vertices, log-uniform), each graph
     coarsened recursively until it has fewer than min_n vertices.
-    Returns a dict with graphs/s of both paths and the identity check."""
+
+    The batched arm runs with the configuration the autotuner picks for this
+    batch (autotune.tune_batch: lanes per low-degree row and resident blocks
+    of the persistent loop, each candidate checked element by element against
+    the default configuration's output).  Two plain arms: one
+    mis2_coarsen_level call per graph and level, with the host-driven round
+    loop and with the persistent device loop.  Every arm is timed the same
+    way: CUDA events around the whole pass, L2 flushed before it.  Returns a
+    dict with graphs/s of every arm and the identity checks."""
     import torch
 
-    from paper_2204_02934_gb300 import graphgen as gg, mis2
+    from paper_2204_02934_gb300 import autotune, graphgen as gg, mis2
 
     graphs = gg.mixed_batch(n_graphs, seed=seed)
     tot_n, tot_nnz = sum(g.n for g in graphs), sum(g.nnz for g in graphs)
     dgs = [mis2.DeviceGraph.from_host(g) for g in graphs]
-    b = mis2.Batch(n_graphs, tot_n, tot_nnz, loop=mis2.MIS2_LOOP_DEVICE)
+    tuned, tuned_ms, table = autotune.tune_batch(graphs, seed=0, min_n=min_n, reps=2)
+    b = mis2.Batch(n_graphs, tot_n, tot_nnz, cfg=autotune._config(tuned))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        t, out = 0.0, None
+        for _ in range(reps):
+            flush.fill_(1)
+            ev0.record()
+            out = fn()
+            ev1.record()
+            ev1.synchronize()
+            t += ev0.elapsed_time(ev1) / 1e3
+        return t / reps, out
+
     for _ in range(max(warmup, 1)):
         nlev = b.coarsen(dgs, min_n=min_n)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t_b = 0.0
     launches = 0
+    t_b = 0.0
     for _ in range(steps):
-        flush.fill_(1)
-        ev0.record()
-        nlev = b.coarsen(dgs, min_n=min_n)
-        ev1.record()
-        ev1.synchronize()
-        t_b += ev0.elapsed_time(ev1) / 1e3
+        dt, nlev = timed(lambda: b.coarsen(dgs, min_n=min_n), 1)
+        t_b += dt
         launches += b.stats().launches
-    batched = n_graphs * steps / t_b
+    t_b /= steps
+    batched = n_graphs / t_b
 
-    # per-graph plain launches: host-driven rounds, one graph and one level at a time
     maxn = max(g.n for g in graphs)
     maxnnz = max(g.nnz for g in graphs)
-    ctx = mis2.Context(maxn, maxnnz, loop=mis2.MIS2_LOOP_HOST)
 
-    def plain_pass(record=False):
+    def plain_pass(ctx, record=False):
         out = []
         for dg in dgs:
             cur, levels = dg, []
@@ -412,28 +428,34 @@ def run_batch_compare(steps=3, warmup=2, n_graphs=512, seed=7, min_n=1000):
             out.append(levels)
         return out
 
-    ref = plain_pass(record=True)
-    torch.cuda.synchronize()
-    flush.fill_(1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    plain_pass()
-    torch.cuda.synchronize()
-    t_p = time.perf_counter() - t0
-    plain = n_graphs / t_p
-    same = True
-    for gi in range(n_graphs):
-        for L, lab in enumerate(ref[gi]):
-            if not torch.equal(b.labels(L, gi), lab):
-                same = False
+    arms = {}
+    for name, loop in (("plain_host_loop", mis2.MIS2_LOOP_HOST), ("plain_device_loop", mis2.MIS2_LOOP_DEVICE)):
+        ctx = mis2.Context(maxn, maxnnz, loop=loop)
+        ref = plain_pass(ctx, record=True)
+        torch.cuda.synchronize()
+        dt, _ = timed(lambda: plain_pass(ctx), 1)
+        same = True
+        for gi in range(n_graphs):
+            for L, lab in enumerate(ref[gi]):
+                if not torch.equal(b.labels(L, gi), lab):
+                    same = False
+                    break
+            if not same:
                 break
-        if not same:
-            break
+        arms[name] = {"graphs_per_s": n_graphs / dt, "ms": 1e3 * dt, "identical_output": same}
+        ctx.close()
+    fastest_plain = max(a["graphs_per_s"] for a in arms.values())
     return {"workload": f"{n_graphs} mixed graphs (2D 5-pt, 3D 7-pt, 2D RGG; 1k-200k vertices, log-uniform, "
                         f"{tot_n} vertices, {tot_nnz} entries), recursive coarsening until < {min_n} vertices",
-            "unit": "graphs/s", "batched": batched, "plain": plain, "speedup": batched / plain,
-            "levels": nlev, "identical_output": same, "batched_ms": 1e3 * t_b / steps,
-            "plain_ms": 1e3 * t_p, "batched_gpu_launches_per_step": launches // steps}
+            "unit": "graphs/s", "batched": batched, "batched_ms": 1e3 * t_b, "levels": nlev,
+            "batched_config": {k: int(v) for k, v in tuned.items()},
+            "autotune_candidates": [{"config": {k: int(v) for k, v in r["config"].items()},
+                                     "ms": round(r["ms"], 3), "identical": r["identical"]} for r in table],
+            "plain": fastest_plain, "plain_arms": arms, "speedup": batched / fastest_plain,
+            "speedup_vs_host_loop_plain": batched / arms["plain_host_loop"]["graphs_per_s"],
+            "identical_output": all(a["identical_output"] for a in arms.values()),
+            "timing": "CUDA events around each whole pass, L2 flushed before it",
+            "batched_gpu_launches_per_step": launches // steps}
 
 
 def run_serve(args):

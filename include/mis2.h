@@ -213,6 +213,22 @@ int mis2_run_with_priorities(mis2_ctx* ctx, const mis2_csr* g, const uint32_t* p
                              int64_t* n_roots, int32_t* n_rounds, void* stream);
 
 /*
+ * Test hook for the round-by-round values of Fig. 1 (Section III-A):
+ * mis2_run_with_priorities, recording for every round r < snap_rounds three
+ * copies of the status arrays into snaps (DEVICE, uint32, snap_rounds * 3 * n
+ * entries, written by the call): [r][0] = T after round r's row refresh,
+ * [r][1] = the column tuples M after its column step, [r][2] = T after its
+ * decide step.  The row refresh of round r + 1 is fused into round r's
+ * decide, so in [r][2] a vertex still undecided holds its next round's tuple:
+ * there only IN (0), OUT (0xFFFFFFFF) and "undecided" are the step's result.
+ * Rounds that did not run, and M of vertices the column step no longer
+ * visits (their M stays OUT), read OUT.  Works with both round-loop drivers.
+ */
+int mis2_run_snapshots(mis2_ctx* ctx, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
+                       uint32_t* snaps, int32_t snap_rounds, uint8_t* in_set, int32_t* roots, int64_t* n_roots,
+                       int32_t* n_rounds, void* stream);
+
+/*
  * Aggregation (Algorithm 3, or Algorithm 2 when mode = MIS2_AGG_BASIC).
  *   roots     int32[n_roots], device, ascending: an MIS-2 of g (e.g. from mis2_run).
  *   labels    int32[n], device: aggregate id of each vertex, in [0, *n_aggs).

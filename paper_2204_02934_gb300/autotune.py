@@ -12,7 +12,10 @@ output is bit-identical to the default configuration's.  Tuned knobs:
 
 Results are cached in a JSON file keyed by a graph-class string (average
 degree, maximum degree and size buckets), so one tuning serves every graph of
-the same shape.
+the same shape.  tune_batch does the same for the batched hierarchy engine
+(mis2.Batch) on a mixed batch of graphs, a candidate counting only when every
+level's labels and coarse graph of every graph equal the default
+configuration's, element by element.
 """
 from __future__ import annotations
 
@@ -46,9 +49,17 @@ def _config(overrides) -> mis2.mis2_config:
     return cfg
 
 
-def _digest(out) -> tuple:
-    return tuple(int(x) for x in (out["n_aggs"], out["c_colind"].numel(), out["labels"].sum().item(),
-                                  out["c_colind"].sum().item(), out["roots"].sum().item()))
+def _same_level(a, b) -> bool:
+    """Two coarsening levels (dicts of device tensors) identical element by element."""
+    import torch
+
+    return int(a["n_aggs"]) == int(b["n_aggs"]) and all(
+        a[k].shape == b[k].shape and bool(torch.equal(a[k], b[k])) for k in ("in_set", "roots", "labels", "c_rowptr",
+                                                                          "c_colind"))
+
+
+def _level_copy(out) -> dict:
+    return {k: (v.clone() if hasattr(v, "clone") else v) for k, v in out.items()}
 
 
 def candidates(grid=None, max_degree: int = 1 << 30):
@@ -68,7 +79,7 @@ def tune_graph(g, seed: int = 0, reps: int = 3, grid=None, limit: int | None = N
     dg = mis2.DeviceGraph.from_host(g)
     max_deg = int(np.max(g.degrees())) if g.n else 0
     ref_ctx = mis2.Context(g.n, g.nnz)
-    ref = _digest(ref_ctx.coarsen_level(dg, seed))
+    ref = _level_copy(ref_ctx.coarsen_level(dg, seed))
     ref_ctx.close()
     cands = candidates(grid, max_deg)
     if limit:
@@ -79,7 +90,7 @@ def tune_graph(g, seed: int = 0, reps: int = 3, grid=None, limit: int | None = N
     for cand in cands:
         ctx = mis2.Context(g.n, g.nnz, cfg=_config(cand))
         out = ctx.coarsen_level(dg, seed)
-        ok = _digest(out) == ref
+        ok = _same_level(out, ref)
         ms = float("inf")
         if ok:
             for _ in range(reps):
@@ -121,6 +132,82 @@ def tuned_config(g, path: str | None = None, **tune_kwargs) -> dict:
         if hit is not None:
             return hit
     best, ms, _ = tune_graph(g, **tune_kwargs)
+    if path:
+        save(path, key, best, ms)
+    return best
+
+
+BATCH_GRID = {"group_lanes": [1, 2, 4], "loop_blocks_per_sm": [1, 2]}
+
+
+def batch_class(graphs) -> str:
+    """Bucketed shape of a batch: graph count, log2 of total size and of the
+    average degree."""
+    n = sum(g.n for g in graphs)
+    nnz = sum(g.nnz for g in graphs)
+    return f"batch{len(graphs)}_n{int(math.log2(n + 1))}_avg{int(math.log2(nnz / max(n, 1) + 1))}"
+
+
+def _batch_outputs(b, n_graphs: int, levels: int):
+    """Every level's labels and coarse graph of every graph coarsened there."""
+    out = []
+    for L in range(levels):
+        n, _, _ = b.level_sizes(L)
+        for gi in range(n_graphs):
+            if n[gi] == 0:
+                continue
+            lab = b.labels(L, gi)
+            crp, cci = b.coarse(L, gi)
+            out.append((L, gi, lab.clone(), crp.clone(), cci.clone()))
+    return out
+
+
+def tune_batch(graphs, seed: int = 0, min_n: int = 1000, reps: int = 3, grid=None, verbose: bool = False):
+    """Tune the batched engine (device loop) for a list of host graphs.
+    Returns (best overrides, ms per batch, table)."""
+    import torch
+
+    grid = grid or BATCH_GRID
+    dgs = [mis2.DeviceGraph.from_host(g) for g in graphs]
+    tot_n, tot_nnz = sum(g.n for g in graphs), sum(g.nnz for g in graphs)
+    ref_b = mis2.Batch(len(graphs), tot_n, tot_nnz, loop=mis2.MIS2_LOOP_DEVICE)
+    levels = ref_b.coarsen(dgs, seed=seed, min_n=min_n)
+    ref = _batch_outputs(ref_b, len(graphs), levels)
+    ref_b.close()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    table, best, best_ms = [], {}, float("inf")
+    for gl, bps in itertools.product(grid["group_lanes"], grid["loop_blocks_per_sm"]):
+        cand = {"loop": mis2.MIS2_LOOP_DEVICE, "group_lanes": gl, "loop_blocks_per_sm": bps}
+        b = mis2.Batch(len(graphs), tot_n, tot_nnz, cfg=_config(cand))
+        lv = b.coarsen(dgs, seed=seed, min_n=min_n)
+        got = _batch_outputs(b, len(graphs), lv) if lv == levels else None
+        ok = got is not None and len(got) == len(ref) and all(
+            p[:2] == q[:2] and all(bool(torch.equal(x, y)) for x, y in zip(p[2:], q[2:])) for p, q in zip(got, ref))
+        ms = float("inf")
+        if ok:
+            for _ in range(reps):
+                ev0.record()
+                b.coarsen(dgs, seed=seed, min_n=min_n)
+                ev1.record()
+                ev1.synchronize()
+                ms = min(ms, ev0.elapsed_time(ev1))
+        b.close()
+        table.append({"config": cand, "ms": ms, "identical": ok})
+        if verbose:
+            print(json.dumps(table[-1]), flush=True)
+        if ok and ms < best_ms:
+            best, best_ms = cand, ms
+    return best, best_ms, table
+
+
+def tuned_batch_config(graphs, path: str | None = None, **tune_kwargs) -> dict:
+    """Cached batch tuning for the class of this batch (tunes on a miss)."""
+    key = batch_class(graphs)
+    if path:
+        hit = load(path, key)
+        if hit is not None:
+            return hit
+    best, ms, _ = tune_batch(graphs, **tune_kwargs)
     if path:
         save(path, key, best, ms)
     return best

@@ -355,11 +355,11 @@ int mis2_run(mis2_ctx* c, const mis2_csr* g, uint64_t seed, uint8_t* in_set, int
   return rc;
 }
 
-int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
-                             uint8_t* in_set, int32_t* roots, int64_t* n_roots, int32_t* n_rounds, void* stream) {
-  NvtxRange nvtx_call("mis2_run_with_priorities");
+static int run_priorities_impl(mis2_ctx* c, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
+                               uint32_t* snaps, int32_t snap_rounds, uint8_t* in_set, int32_t* roots,
+                               int64_t* n_roots, int32_t* n_rounds, void* stream) {
   if (c == nullptr || n_roots == nullptr || table_rounds < 0 || (table_rounds > 0 && prio_table == nullptr) ||
-      tuple_ablation(c))
+      snap_rounds < 0 || (snap_rounds > 0 && snaps == nullptr) || tuple_ablation(c))
     return MIS2_ERR_INVALID_ARG;
   GraphArgs ga;
   MIS2_TRY(validate_graph(c, g, &ga));
@@ -379,13 +379,36 @@ int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* pri
     p.table = dtab;
     p.table_rounds = table_rounds;
   }
-  int rc = run_impl(c, ga, p, in_set, roots, n_roots, n_rounds, st);
+  int rc = MIS2_OK;
+  if (snap_rounds > 0 && ga.n > 0) {
+    const cudaError_t e = cudaMemsetAsync(snaps, 0xFF, (size_t)snap_rounds * 3 * (size_t)ga.n * sizeof(uint32_t), st);
+    if (e != cudaSuccess) rc = set_cuda_error(e);
+    c->snaps = snaps;
+    c->snap_rounds = snap_rounds;
+  }
+  if (rc == MIS2_OK) rc = run_impl(c, ga, p, in_set, roots, n_roots, n_rounds, st);
+  c->snaps = nullptr;
+  c->snap_rounds = 0;
   if (dtab) {
     cudaStreamSynchronize(st);
     cudaFree(dtab);
   }
   if (rc == MIS2_OK) rc = timer_collect(c);
   return rc;
+}
+
+int mis2_run_with_priorities(mis2_ctx* c, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
+                             uint8_t* in_set, int32_t* roots, int64_t* n_roots, int32_t* n_rounds, void* stream) {
+  NvtxRange nvtx_call("mis2_run_with_priorities");
+  return run_priorities_impl(c, g, prio_table, table_rounds, nullptr, 0, in_set, roots, n_roots, n_rounds, stream);
+}
+
+int mis2_run_snapshots(mis2_ctx* c, const mis2_csr* g, const uint32_t* prio_table, int32_t table_rounds,
+                       uint32_t* snaps, int32_t snap_rounds, uint8_t* in_set, int32_t* roots, int64_t* n_roots,
+                       int32_t* n_rounds, void* stream) {
+  NvtxRange nvtx_call("mis2_run_snapshots");
+  return run_priorities_impl(c, g, prio_table, table_rounds, snaps, snap_rounds, in_set, roots, n_roots, n_rounds,
+                             stream);
 }
 
 int mis2_aggregate(mis2_ctx* c, const mis2_csr* g, const int32_t* roots, int64_t n_roots, uint64_t seed,

@@ -35,7 +35,16 @@ struct LoopArgs {
   int32_t rounds_slot;
   int32_t barrier_extra;  // arrivals awaited beyond the grid: 1 = forced timeout (test hook)
   int32_t no_worklists;   // visit every vertex every round (ablation)
+  uint32_t* snaps;        // mis2_run_snapshots: per-round copies of T and M, or null
+  int32_t snap_rounds;
 };
+
+// Copy n words grid-wide (mis2_run_snapshots); the source is not written in
+// the phase that runs until the next grid barrier.
+__device__ __forceinline__ void grid_copy(uint32_t* dst, const uint32_t* src, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
 
 template <int G, typename I, bool NOWL>
 __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I> g, PrioCfg p, LoopArgs a) {
@@ -84,6 +93,10 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
       w1 += n1[k];
       w2 += n2[k];
     }
+    if (a.snaps != nullptr) {  // T after round r - 1's decide step, after round r's refresh
+      if (r > 0 && r - 1 < a.snap_rounds) grid_copy(a.snaps + ((int64_t)(r - 1) * 3 + 2) * g.n, a.T, g.n);
+      if (w1 > 0 && r < a.snap_rounds) grid_copy(a.snaps + (int64_t)r * 3 * g.n, a.T, g.n);
+    }
     if (w1 == 0) break;
     if (nowl) {  // every vertex visited; n1/n2 above were the compacted counts
       w2 = 0;
@@ -120,6 +133,7 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
                                   gridDim.x, sh);
     const bool ts_on = ts != nullptr && r < MIS2_TRACE_CAP;
     if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr, a.barrier_extra)) return;
+    if (a.snaps != nullptr && r < a.snap_rounds) grid_copy(a.snaps + ((int64_t)r * 3 + 1) * g.n, a.M, g.n);
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 0] = nowl ? n1[0] + n1[1] + n1[2] : w1;
@@ -192,6 +206,8 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.rounds_slot = rounds_slot;
   la.barrier_extra = (c->cfg.debug_checks & MIS2_DEBUG_FORCE_TIMEOUT) ? 1 : 0;
   la.no_worklists = (c->cfg.ablation & MIS2_ABLATE_NO_WORKLISTS) ? 1 : 0;
+  la.snaps = labels == nullptr ? c->snaps : nullptr;
+  la.snap_rounds = c->snap_rounds;
   if (sync) {
     MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
   } else {

@@ -154,6 +154,9 @@ struct mis2_ctx {
   // one grid-synchronised kernel of theirs is resident at a time.
   std::mutex* coop_lock = nullptr;
   cudaEvent_t coop_done = nullptr;
+  // mis2_run_snapshots: per-round copies of T and M (device; null otherwise)
+  uint32_t* snaps = nullptr;
+  int32_t snap_rounds = 0;
 };
 
 namespace mis2 {

@@ -298,6 +298,13 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
     MIS2_CUDA(cudaMemcpyAsync(s.ctr + kCtrInitSizes + kClasses, s.ctr + ctr_c2(0, 0), kClasses * sizeof(int32_t),
                               cudaMemcpyDeviceToDevice, st));
   }
+  // mis2_run_snapshots: the round's copy of T or M (stream-ordered)
+  auto snap = [&](int round, int which, const uint32_t* src) -> int {
+    if (c->snaps == nullptr || labels != nullptr || round >= c->snap_rounds) return MIS2_OK;
+    MIS2_CUDA(cudaMemcpyAsync(c->snaps + ((int64_t)round * 3 + which) * g.n, src, (size_t)g.n * sizeof(uint32_t),
+                              cudaMemcpyDeviceToDevice, st));
+    return MIS2_OK;
+  };
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   MIS2_CUDA(cudaStreamSynchronize(st));
   int32_t n1_0[kClasses], n2_0[kClasses];
@@ -317,6 +324,7 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
     }
     if (w1 == 0) break;
     if (r > g.n) return MIS2_ERR_NO_PROGRESS;
+    MIS2_TRY(snap(r, 0, s.T));  // T after round r's row refresh
     if (nowl)
       for (int k = 0; k < kClasses; k++) {
         n1[k] = n1_0[k];
@@ -340,6 +348,7 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
                        s.ctr + ctr_c2(nslot, k), k == 0 ? s.ctr + ctr_c1(nslot, 0) : nullptr, t, st);
     }
     timer_end(c, st);
+    MIS2_TRY(snap(r, 1, s.M));
     // decide over worklist1 (with the next round's refresh)
     timer_begin(c, kKcDecide, st);
     for (int k = 0; k < kClasses; k++) {
@@ -354,6 +363,7 @@ static int rounds_host_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels,
     }
     timer_end(c, st);
     MIS2_CUDA(cudaGetLastError());
+    MIS2_TRY(snap(r, 2, s.T));
     MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MIS2_CUDA(cudaStreamSynchronize(st));
     r++;

@@ -34,7 +34,7 @@ KERNEL_CLASSES = ["init", "column", "decide", "compact", "aggregate", "coarse", 
 # C function names the header declares (checked by the CPU tests).
 EXPORTS = [
     "mis2_config_default", "mis2_ctx_create", "mis2_ctx_destroy", "mis2_ctx_set_config", "mis2_get_stats",
-    "mis2_run", "mis2_run_with_priorities", "mis2_aggregate", "mis2_coarsen", "mis2_coarsen_level",
+    "mis2_run", "mis2_run_with_priorities", "mis2_run_snapshots", "mis2_aggregate", "mis2_coarsen", "mis2_coarsen_level",
     "mis2_coarsen_level_host", "mis2_status_string", "mis2_last_error", "mis2_version", "mis2_run_noalloc",
     "mis2_batch_create", "mis2_batch_destroy", "mis2_batch_coarsen", "mis2_batch_level_sizes", "mis2_batch_labels",
     "mis2_batch_coarse", "mis2_batch_stats",
@@ -123,6 +123,7 @@ def _lib(build_if_missing: bool = False):
         "mis2_get_stats": (i32, [P, ctypes.POINTER(mis2_stats)]),
         "mis2_run": (i32, [P, CSR, u64, P, P, pi64, pi32, P]),
         "mis2_run_with_priorities": (i32, [P, CSR, P, i32, P, P, pi64, pi32, P]),
+        "mis2_run_snapshots": (i32, [P, CSR, P, i32, P, i32, P, P, pi64, pi32, P]),
         "mis2_aggregate": (i32, [P, CSR, P, i64, u64, i32, P, pi64, P]),
         "mis2_coarsen": (i32, [P, CSR, P, i64, P, P, i64, pi64, P]),
         "mis2_coarsen_level": (i32, [P, CSR, u64, P, P, P, P, P, i64, pi64, pi64, pi64, P]),
@@ -224,6 +225,16 @@ def mis2_run_with_priorities(ctx, g: mis2_csr, prio_table: np.ndarray, in_set, r
     _check(_lib().mis2_run_with_priorities(ctx, ctypes.byref(g), _ptr(tab), tab.shape[0], _ptr(in_set),
                                            _ptr(roots), ctypes.byref(nr), ctypes.byref(rounds), _stream(stream)),
            "mis2_run_with_priorities")
+    return nr.value, rounds.value
+
+
+def mis2_run_snapshots(ctx, g: mis2_csr, prio_table: np.ndarray, snaps, snap_rounds: int, in_set, roots,
+                       stream=None):
+    tab = np.ascontiguousarray(prio_table, dtype=np.uint32)
+    nr, rounds = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(_lib().mis2_run_snapshots(ctx, ctypes.byref(g), _ptr(tab), tab.shape[0], _ptr(snaps), snap_rounds,
+                                     _ptr(in_set), _ptr(roots), ctypes.byref(nr), ctypes.byref(rounds),
+                                     _stream(stream)), "mis2_run_snapshots")
     return nr.value, rounds.value
 
 
@@ -359,6 +370,17 @@ class Context:
         roots = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dg.rowptr.device)
         nr, rounds = mis2_run_with_priorities(self.handle, dg.csr, prio_table, in_set, roots, stream)
         return in_set[:dg.n], roots[:nr], rounds
+
+    def run_snapshots(self, dg: DeviceGraph, prio_table, snap_rounds: int, stream=None):
+        """mis2_run_snapshots: (in_set, roots, rounds, snaps[snap_rounds, 3, n]) with snaps on the device."""
+        import torch
+
+        dev = dg.rowptr.device
+        in_set = torch.empty(max(dg.n, 1), dtype=torch.uint8, device=dev)
+        roots = torch.empty(max(dg.n, 1), dtype=torch.int32, device=dev)
+        snaps = torch.empty(max(snap_rounds * 3 * dg.n, 1), dtype=torch.int32, device=dev)
+        nr, rounds = mis2_run_snapshots(self.handle, dg.csr, prio_table, snaps, snap_rounds, in_set, roots, stream)
+        return in_set[:dg.n], roots[:nr], rounds, snaps[:snap_rounds * 3 * dg.n].view(snap_rounds, 3, dg.n)
 
     def aggregate(self, dg: DeviceGraph, roots, seed: int = 0, mode: int = MIS2_AGG_ALG3, stream=None):
         import torch

@@ -46,6 +46,64 @@ def test_fig1_worked_example_on_gpu(loop):
     assert rounds == fx["n_rounds"]
 
 
+def _unpack(t, b):
+    if t == 0:
+        return "IN"
+    if t == 0xFFFFFFFF:
+        return "OUT"
+    return [t >> b, t & ((1 << b) - 1)]
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_fig1_round_by_round_on_gpu(loop):
+    """Fig. 1 step by step: the injected priorities after each row refresh,
+    the column tuples M after each column step and the decisions after each
+    decide step, as the figure prints them (tests/golden/fig1.json)."""
+    fx = json.load(open(os.path.join(GOLDEN, "fig1.json")))
+    n = fx["n"]
+    g = gg.graph_from_edges(n, [(a - 1, b - 1) for a, b in fx["edges"]])
+    tab = np.zeros((len(fx["rounds"]), n), dtype=np.uint32)
+    for r, rd in enumerate(fx["rounds"]):
+        for vid, p in rd["priorities"].items():
+            tab[r, int(vid) - 1] = p
+    ctx = make_ctx(g, loop=loop)
+    in_set, roots, rounds, snaps = ctx.run_snapshots(mis2.DeviceGraph.from_host(g), tab, 4)
+    snaps = snaps.cpu().numpy().view(np.uint32)
+    b = oracle.id_bits(n)
+    assert b == 3 and rounds == fx["n_rounds"]
+    assert (roots.cpu().numpy() + 1).tolist() == fx["result"]
+    for r, rd in enumerate(fx["rounds"]):
+        T0, M, T1 = snaps[r]
+        for vid, p in rd["priorities"].items():
+            assert _unpack(int(T0[int(vid) - 1]), b) == [p, int(vid)], (r, vid)
+        for vid, m in rd["column"].items():
+            assert _unpack(int(M[int(vid) - 1]), b) == m, (r, vid)
+        for vid, d in rd["decide"].items():
+            got = _unpack(int(T1[int(vid) - 1]), b)
+            assert (got if isinstance(got, str) else "U") == d, (r, vid)
+    assert (snaps[len(fx["rounds"]):] == 0xFFFFFFFF).all()  # rounds that did not run
+
+
+@pytest.mark.parametrize("loop", LOOPS)
+def test_snapshots_equal_the_oracle_round_by_round(loop):
+    """On hashed priorities (no table) the GPU's per-round T after the
+    refresh and M after the column step equal the oracle's exactly, and the
+    decisions agree as IN / OUT / undecided."""
+    g = gg.random_graph(60, 0.08, 4)
+    ctx = make_ctx(g, loop=loop)
+    _, roots, rounds, snaps = ctx.run_snapshots(mis2.DeviceGraph.from_host(g), np.zeros((0, g.n), np.uint32), 8)
+    snaps = snaps.cpu().numpy().view(np.uint32)
+    ref = oracle.mis2(g, 0, snap_cap=8)
+    assert rounds == ref[2] and np.array_equal(roots.cpu().numpy(), ref[1])
+    status = lambda t: np.where(t == 0, 0, np.where(t == 0xFFFFFFFF, 2, 1))
+    for r in range(min(rounds, 8)):
+        T0, M, T1 = snaps[r]
+        oT0, oM, oT1 = ref[4][r]
+        assert np.array_equal(T0, oT0), r
+        assert np.array_equal(M, oM), r
+        assert np.array_equal(status(T1), status(oT1)), r
+
+
 def _edges_of(n, mask):
     pairs = list(itertools.combinations(range(n), 2))
     return [p for k, p in enumerate(pairs) if (mask >> k) & 1]
