@@ -458,14 +458,20 @@ def run_batch_compare(steps=3, warmup=2, n_graphs=512, seed=7, min_n=1000):
             "batched_gpu_launches_per_step": launches // steps}
 
 
-def run_serve(args):
+def serve_compare(requests=20000, rate=2000.0, slots=4, batch_max=16, sat_requests=4000, below_requests=4000,
+                  loop="device"):
     """Serving: a Poisson stream of one-level requests (H2D of the CSR, MIS-2,
     aggregation, coarse graph, D2H of every output) drawn from a pool of 64
     pinned-host graphs (3D 7-pt grids of side 20-160 and R-MAT graphs of scale
-    14-20, average degree 16).  Serial plain launches (one request at a time)
-    against continuous batching over `--slots` resident slots; p50/p99 latency
-    at the offered rate, saturation throughput with every request queued at
-    once, and the identity of each request's result alone and in the mix."""
+    14-20, average degree 16).  Three servers: serial plain launches (one
+    slot, one request at a time), `slots` slots of one request each, and
+    merged launches (two slots, each running up to `batch_max` queued
+    requests as one union through the batched engine).  Per server: p50/p99
+    latency at the offered rate, throughput with every request queued at once
+    (saturation), and p50/p99 at 50 % and 80 % of the merged server's
+    saturation rate (below saturation, so latency is service time plus short
+    queueing); each request's result fingerprint must be the same in every
+    server."""
     from paper_2204_02934_gb300 import graphgen as gg
 
     t_gen = time.perf_counter()
@@ -485,11 +491,11 @@ def run_serve(args):
         host.append(mis2.mis2_csr(g.n, g.nnz, 1 if rp.dtype == torch.int64 else 0, 0, rp.data_ptr(),
                                   ci.data_ptr() if g.nnz else None))
     max_n, max_nnz = max(g.n for g in pool), max(g.nnz for g in pool)
-    n_req, rate = args.requests, args.rate
-    arrivals = gg.poisson_arrivals(n_req, rate, seed=13)
-    idx = np.minimum((gg.uniform01(np.arange(n_req, dtype=np.uint64), 17) * len(pool)).astype(np.int32),
+    arrivals = gg.poisson_arrivals(requests, rate, seed=13)
+    idx = np.minimum((gg.uniform01(np.arange(requests, dtype=np.uint64), 17) * len(pool)).astype(np.int32),
                      len(pool) - 1)
-    n_sat = min(n_req, args.saturation_requests)
+    n_sat = min(requests, sat_requests)
+    n_below = min(requests, below_requests)
 
     def summarize(res, t_first):
         lat = np.array([r.t_done - r.t_arrive for r in res])
@@ -499,10 +505,12 @@ def run_serve(args):
                 "p99_ms": 1e3 * float(np.percentile(lat, 99)), "mean_ms": 1e3 * float(lat.mean()),
                 "service_mean_ms": 1e3 * float(svc.mean())}
 
-    out, sums = {}, {}
-    for name, slots in (("serial", 1), ("continuous", args.slots)):
-        srv = mis2.Server(slots=slots, slot_max_n=max_n, slot_max_nnz=max_nnz, mem_budget=64 << 30,
-                          loop=mis2.MIS2_LOOP_DEVICE if args.loop == "device" else mis2.MIS2_LOOP_HOST)
+    servers = (("serial", 1, 0, max_n, max_nnz), ("slots", slots, 0, max_n, max_nnz),
+               ("merged", 2, batch_max, max(4 * max_n, 1 << 22), max(4 * max_nnz, 1 << 26)))
+    out, sums, handles = {}, {}, {}
+    for name, sl, bm, sn, snnz in servers:
+        srv = mis2.Server(slots=sl, slot_max_n=sn, slot_max_nnz=snnz, mem_budget=96 << 30, batch_max=bm,
+                          loop=mis2.MIS2_LOOP_DEVICE if loop == "device" else mis2.MIS2_LOOP_HOST)
         srv.replay(host, np.zeros(len(pool)), np.arange(len(pool), dtype=np.int32), seed=0)  # warm-up
         res, mif = srv.replay(host, arrivals, idx, seed=0)
         if any(r.status != 0 for r in res):
@@ -514,30 +522,49 @@ def run_serve(args):
         sat = summarize(res2, min(r.t_arrive for r in res2))
         sat["max_in_flight"] = mif2
         sums[name + "_sat"] = [r.checksum for r in res2]
+        out[name] = {"slots": sl, "batch_max": bm, "open_loop": open_loop, "saturation": sat}
+        handles[name] = srv
+    sat_rate = out["merged"]["saturation"]["graphs_per_s"]
+    for name, srv in handles.items():
+        below = {}
+        for frac in (0.5, 0.8):
+            arr = gg.poisson_arrivals(n_below, frac * sat_rate, seed=29)
+            res3, mif3 = srv.replay(host, arr, idx[:n_below], seed=0)
+            sm = summarize(res3, min(r.t_arrive for r in res3))
+            sm.update(offered_req_per_s=round(frac * sat_rate, 1), max_in_flight=mif3)
+            below[f"{int(frac * 100)}pct_of_merged_saturation"] = sm
+            sums.setdefault(name + "_below", []).extend(r.checksum for r in res3)
+        out[name]["below_saturation"] = below
         srv.close()
-        out[name] = {"slots": slots, "open_loop": open_loop, "saturation": sat}
-    same = sums["serial"] == sums["continuous"] and sums["serial_sat"] == sums["continuous_sat"]
+    same = all(sums[k] == sums["serial" + k[len(k.split("_")[0]):]] for k in sums)
     per_graph = {}
     for i, h in zip(idx, sums["serial"]):
         per_graph.setdefault(int(i), set()).add(h)
     same = same and all(len(v) == 1 for v in per_graph.values())
-    line = {
-        "metric": "serving graphs/s at saturation and p50/p99 latency at the offered rate (one coarsening level "
-                  "per request, H2D + compute + D2H)",
-        "value": round(out["continuous"]["saturation"]["graphs_per_s"], 1), "unit": "graphs/s",
-        "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"{n_req} requests, Poisson arrivals at {rate:g} req/s (seed 13), drawn uniformly "
-                               f"from 64 pinned-host graphs (3D 7-pt side log-uniform 20-160 / R-MAT scale 14-20, "
-                               f"avg degree 16, seed 11; {sum(g.nnz for g in pool)} entries in the pool); "
-                               f"saturation: {n_sat} requests queued at t=0",
-                   "slots": args.slots, "loop": args.loop},
-        "serial": out["serial"], "continuous": out["continuous"],
-        "speedup_vs_serial": {"saturation": out["continuous"]["saturation"]["graphs_per_s"] /
-                              out["serial"]["saturation"]["graphs_per_s"],
-                              "p99_at_offered_rate": out["serial"]["open_loop"]["p99_ms"] /
-                              out["continuous"]["open_loop"]["p99_ms"]},
+    return {
+        "workload": f"{requests} requests, Poisson arrivals at {rate:g} req/s (seed 13), drawn uniformly from 64 "
+                    f"pinned-host graphs (3D 7-pt side log-uniform 20-160 / R-MAT scale 14-20, avg degree 16, seed "
+                    f"11; {sum(g.nnz for g in pool)} entries in the pool); saturation: {n_sat} requests queued at "
+                    f"t=0; below saturation: {n_below} requests at 50 % and 80 % of the merged server's saturation",
+        "unit": "graphs/s", "loop": loop,
+        "serial": out["serial"], "slots": out["slots"], "merged": out["merged"],
+        "speedup_vs_serial_at_saturation": {k: out[k]["saturation"]["graphs_per_s"] /
+                                            out["serial"]["saturation"]["graphs_per_s"] for k in ("slots", "merged")},
         "identical_output": bool(same), "pool_generation_s": round(t_gen, 1),
     }
+
+
+def run_serve(args):
+    """--workload serve: serve_compare at the command line's sizes, one JSON line."""
+    sc = serve_compare(args.requests, args.rate, args.slots, args.batch_max, args.saturation_requests,
+                       args.below_requests, args.loop)
+    line = {"metric": "serving graphs/s at saturation and p50/p99 latency (one coarsening level per request, "
+                      "H2D + compute + D2H)",
+            "value": round(sc["merged"]["saturation"]["graphs_per_s"], 1), "unit": "graphs/s",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": sc["workload"], "slots": args.slots, "batch_max": args.batch_max,
+                       "loop": args.loop},
+            **{k: v for k, v in sc.items() if k not in ("workload",)}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -766,6 +793,8 @@ def main():
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
     ap.add_argument("--slots", type=int, default=4, help="serve: continuous-batching slots")
     ap.add_argument("--saturation-requests", type=int, default=4000)
+    ap.add_argument("--below-requests", type=int, default=4000, help="serve: requests per below-saturation rate")
+    ap.add_argument("--batch-max", type=int, default=16, help="serve: requests per merged launch")
     args = ap.parse_args()
     if args.workload == "serve":
         return run_serve(args)

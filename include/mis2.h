@@ -393,10 +393,14 @@ int mis2_batch_stats(const mis2_batch* b, mis2_stats* out);
 typedef struct mis2_server mis2_server;
 
 typedef struct {
-  int32_t slots;          /* concurrent requests (default 4) */
-  int32_t reserved;
+  int32_t slots;          /* concurrent launches (default 4) */
+  int32_t batch_max;      /* requests merged into one launch by a slot: 0 or 1 = one request per slot
+                             (its own context); >= 2 = the queued requests that fit (same seed, at most
+                             batch_max of them, slot_max_n / slot_max_nnz in total) run together as one
+                             block-diagonal union through the batched engine (mis2_batch_coarsen, one
+                             level) */
   int64_t mem_budget;     /* bytes of request buffers admitted at once (default 8 GiB) */
-  int64_t slot_max_n;     /* largest request per slot (vertices, entries) */
+  int64_t slot_max_n;     /* largest request (batch_max >= 2: largest union) per slot (vertices, entries) */
   int64_t slot_max_nnz;
   mis2_config cfg;        /* per-slot configuration (default loop: MIS2_LOOP_DEVICE; the slots
                              share a lock so that one device-loop kernel runs at a time, the
@@ -420,6 +424,20 @@ typedef struct {
   int32_t slot;
 } mis2_result;
 
+/* Host buffers that receive a request's results (any may be NULL: not
+ * returned).  in_set[n], roots[n], labels[n], c_rowptr[n+1], c_colind
+ * [c_colind_cap]: the outputs of mis2_coarsen_level_host for the request's
+ * graph; a coarse graph larger than c_colind_cap fails the request with
+ * MIS2_ERR_INVALID_ARG.  They must stay valid until the request completes. */
+typedef struct {
+  uint8_t* in_set;
+  int32_t* roots;
+  int32_t* labels;
+  int32_t* c_rowptr;
+  int32_t* c_colind;
+  int64_t c_colind_cap;
+} mis2_request_out;
+
 void mis2_server_config_default(mis2_server_config* cfg);
 /* Creates cfg->slots contexts (cudaMalloc now) and their worker threads. */
 int mis2_server_create(mis2_server** s, const mis2_server_config* cfg);
@@ -428,6 +446,10 @@ int mis2_server_destroy(mis2_server* s);
 /* Queue one request; g_host points to HOST memory that must stay valid until
  * the request completes.  *ticket (host) identifies it.  Does not block. */
 int mis2_server_submit(mis2_server* s, const mis2_csr* g_host, uint64_t seed, int64_t* ticket);
+/* mis2_server_submit, with the request's results also written to *out's
+ * host buffers (out may be NULL: results as fingerprint only). */
+int mis2_server_submit_out(mis2_server* s, const mis2_csr* g_host, uint64_t seed, const mis2_request_out* out,
+                           int64_t* ticket);
 /* Block until request `ticket` completes; *out (host) receives its result. */
 int mis2_server_wait(mis2_server* s, int64_t ticket, mis2_result* out);
 /* Withdraw request `ticket` if it is still queued: *cancelled (host) = 1 and

@@ -144,6 +144,8 @@ struct BatchLevel {
   int32_t* c_colind = nullptr;
   int64_t cap_labels = 0, cap_crp = 0, cap_cci = 0;
   int32_t rounds = 0, rounds2 = 0;
+  std::vector<int64_t> r1off;    // per live graph (+1 entry): first union root of the graph
+  std::vector<int64_t> ebounds;  // per live graph: [first, end) coarse entry of its rows
 };
 
 struct mis2_batch {
@@ -355,6 +357,7 @@ int mis2_batch_coarsen(mis2_batch* b, int32_t n_graphs, const mis2_csr* graphs, 
     MIS2_CUDA(cudaStreamSynchronize(st));
     // per graph: phase-1 and phase-2 aggregates, aggregate offsets
     std::vector<int64_t> n1(nl), nq(nl), naggs(nl);
+    L.r1off.assign(tab + kTabR1 * tg, tab + kTabR1 * tg + nl + 1);
     L.aggoff.assign(nl + 1, 0);
     for (int i = 0; i < nl; i++) {
       n1[i] = tab[kTabR1 * tg + i + 1] - tab[kTabR1 * tg + i];
@@ -393,6 +396,7 @@ int mis2_batch_coarsen(mis2_batch* b, int32_t n_graphs, const mis2_csr* graphs, 
     MIS2_CUDA(cudaStreamSynchronize(st));
     std::vector<int64_t> ebl(2 * nl);
     for (int j = 0; j < 2 * nl; j++) ebl[j] = tab[kTabSrcA * tg + j];
+    L.ebounds = ebl;
     // record sizes per input graph
     b->lvl_n.emplace_back(n_graphs, 0);
     b->lvl_naggs.emplace_back(n_graphs, 0);
@@ -535,3 +539,30 @@ int mis2_batch_stats(const mis2_batch* b, mis2_stats* out) {
 }
 
 }  // extern "C"
+
+namespace mis2 {
+
+mis2_ctx* batch_context(mis2_batch* b) { return b->ctx; }
+
+int batch_level0_result(const mis2_batch* b, int32_t graph, int32_t* roots, int32_t* labels, int32_t* c_rowptr,
+                        int32_t* c_colind, int64_t* n_roots, int64_t* n_aggs, int64_t* c_nnz, cudaStream_t st) {
+  int li = 0;
+  MIS2_TRY(find_live(b, 0, graph, &li));
+  const BatchLevel& L = b->levels[0];
+  const int64_t v0 = L.voff[li], n = L.voff[li + 1] - v0;
+  const int64_t a0 = L.aggoff[li], na = L.aggoff[li + 1] - a0;
+  const int64_t r0 = L.r1off[li], nr = L.r1off[li + 1] - r0;
+  const int64_t e0 = L.ebounds[2 * li], ne = L.ebounds[2 * li + 1] - e0;
+  if (nr > 0)
+    k_sub_copy<<<grid_for(b->ctx, nr, kBlock), kBlock, 0, st>>>(b->ctx->s.roots_tmp + r0, nr, v0, roots);
+  if (n > 0) k_sub_copy<<<grid_for(b->ctx, n, kBlock), kBlock, 0, st>>>(L.labels + v0, n, a0, labels);
+  k_sub_copy<<<grid_for(b->ctx, na + 1, kBlock), kBlock, 0, st>>>(L.c_rowptr + a0, na + 1, e0, c_rowptr);
+  if (ne > 0) k_sub_copy<<<grid_for(b->ctx, ne, kBlock), kBlock, 0, st>>>(L.c_colind + e0, ne, a0, c_colind);
+  MIS2_CUDA(cudaGetLastError());
+  *n_roots = nr;
+  *n_aggs = na;
+  *c_nnz = ne;
+  return MIS2_OK;
+}
+
+}  // namespace mis2

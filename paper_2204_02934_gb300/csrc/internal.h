@@ -294,6 +294,15 @@ int run_impl(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, uint8_t* in_set,
              int64_t* n_roots, int32_t* n_rounds, cudaStream_t st);
 
 PrioCfg make_prio(const mis2_ctx* c, int64_t n, uint64_t seed);
+
+// Batched engine internals for the server's merged launches.  After a
+// one-level mis2_batch_coarsen: graph `graph`'s roots (ascending), labels,
+// coarse rowptr and colind, renumbered to the graph's own ids, copied into
+// the given device arrays on `st` (asynchronously), with their counts.
+// MIS2_ERR_INVALID_ARG for a graph that was not coarsened (n below min_n).
+mis2_ctx* batch_context(mis2_batch* b);
+int batch_level0_result(const mis2_batch* b, int32_t graph, int32_t* roots, int32_t* labels, int32_t* c_rowptr,
+                        int32_t* c_colind, int64_t* n_roots, int64_t* n_aggs, int64_t* c_nnz, cudaStream_t st);
 int coarse_bitmap_blocks(const mis2_ctx* c);
 
 }  // namespace mis2

@@ -39,6 +39,7 @@ EXPORTS = [
     "mis2_batch_create", "mis2_batch_destroy", "mis2_batch_coarsen", "mis2_batch_level_sizes", "mis2_batch_labels",
     "mis2_batch_coarse", "mis2_batch_stats",
     "mis2_server_config_default", "mis2_server_create", "mis2_server_destroy", "mis2_server_submit",
+    "mis2_server_submit_out",
     "mis2_server_wait", "mis2_server_cancel", "mis2_server_replay", "mis2_coarse_weights", "mis2_tentative_prolongator",
     "mis2_run_k", "mis2_color", "mis2_cluster_lists",
 ]
@@ -71,8 +72,13 @@ class mis2_config(ctypes.Structure):
 
 
 class mis2_server_config(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_int32), ("reserved", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
+    _fields_ = [("slots", ctypes.c_int32), ("batch_max", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
                 ("slot_max_n", ctypes.c_int64), ("slot_max_nnz", ctypes.c_int64), ("cfg", mis2_config)]
+
+
+class mis2_request_out(ctypes.Structure):
+    _fields_ = [("in_set", ctypes.c_void_p), ("roots", ctypes.c_void_p), ("labels", ctypes.c_void_p),
+                ("c_rowptr", ctypes.c_void_p), ("c_colind", ctypes.c_void_p), ("c_colind_cap", ctypes.c_int64)]
 
 
 class mis2_result(ctypes.Structure):
@@ -140,6 +146,7 @@ def _lib(build_if_missing: bool = False):
         "mis2_server_create": (i32, [ctypes.POINTER(P), ctypes.POINTER(mis2_server_config)]),
         "mis2_server_destroy": (i32, [P]),
         "mis2_server_submit": (i32, [P, CSR, u64, pi64]),
+        "mis2_server_submit_out": (i32, [P, CSR, u64, ctypes.POINTER(mis2_request_out), pi64]),
         "mis2_server_wait": (i32, [P, i64, ctypes.POINTER(mis2_result)]),
         "mis2_server_cancel": (i32, [P, i64, pi32]),
         "mis2_server_replay": (i32, [P, i32, CSR, i64, P, P, u64, ctypes.POINTER(mis2_result), pi64]),
@@ -615,6 +622,13 @@ def mis2_server_submit(s, g_host: mis2_csr, seed: int = 0) -> int:
     return t.value
 
 
+def mis2_server_submit_out(s, g_host: mis2_csr, seed: int, out: mis2_request_out) -> int:
+    t = ctypes.c_int64(0)
+    _check(_lib().mis2_server_submit_out(s, ctypes.byref(g_host), seed, ctypes.byref(out), ctypes.byref(t)),
+           "mis2_server_submit_out")
+    return t.value
+
+
 def mis2_server_wait(s, ticket: int) -> mis2_result:
     r = mis2_result()
     _check(_lib().mis2_server_wait(s, ticket, ctypes.byref(r)), "mis2_server_wait")
@@ -643,9 +657,11 @@ def mis2_server_replay(s, pool, arrival_s, pool_index, seed: int = 0):
 class Server:
     """Owns a mis2_server (continuous-batching request loop)."""
 
-    def __init__(self, slots=4, mem_budget=8 << 30, slot_max_n=1 << 22, slot_max_nnz=1 << 25, **cfg_overrides):
+    def __init__(self, slots=4, mem_budget=8 << 30, slot_max_n=1 << 22, slot_max_nnz=1 << 25, batch_max=0,
+                 **cfg_overrides):
         c = mis2_server_config_default()
         c.slots, c.mem_budget, c.slot_max_n, c.slot_max_nnz = slots, mem_budget, slot_max_n, slot_max_nnz
+        c.batch_max = batch_max
         for k, v in cfg_overrides.items():
             setattr(c.cfg, k, v)
         self.cfg = c
@@ -668,6 +684,17 @@ class Server:
     def submit(self, g_host: mis2_csr, seed: int = 0) -> int:
         """Queue one request (g_host must stay valid until it completes)."""
         return mis2_server_submit(self.handle, g_host, seed)
+
+    def submit_out(self, g_host: mis2_csr, n: int, nnz: int, seed: int = 0):
+        """Queue one request whose results are written to fresh numpy arrays:
+        returns (ticket, arrays dict: in_set, roots, labels, c_rowptr, c_colind;
+        valid once wait(ticket) returns, trimmed with the result's counts)."""
+        bufs = {"in_set": np.zeros(max(n, 1), np.uint8), "roots": np.zeros(max(n, 1), np.int32),
+                "labels": np.zeros(max(n, 1), np.int32), "c_rowptr": np.zeros(n + 1, np.int32),
+                "c_colind": np.zeros(max(nnz, 1), np.int32)}
+        out = mis2_request_out(*(b.ctypes.data for b in bufs.values()), max(nnz, 1))
+        t = mis2_server_submit_out(self.handle, g_host, seed, out)
+        return t, bufs
 
     def wait(self, ticket: int) -> mis2_result:
         return mis2_server_wait(self.handle, ticket)

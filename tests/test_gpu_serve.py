@@ -60,24 +60,82 @@ def _pool():
 
 @pytest.mark.parametrize("loop", [mis2.MIS2_LOOP_DEVICE, mis2.MIS2_LOOP_HOST])
 def test_results_same_alone_and_in_the_mix(loop):
+    """One slot (alone), four slots, and two slots merging up to eight queued
+    requests into one union launch: the same fingerprint per request, the
+    oracle's."""
     graphs, keep, host = _pool()
     n_req = 80
     idx = (np.arange(n_req) * 7) % len(graphs)
     arrivals = gg.poisson_arrivals(n_req, 2000.0, seed=4)
     expect = [_oracle_checksum(g, 3)[0] for g in graphs]
     results = {}
-    for slots in (1, 4):
-        srv = mis2.Server(slots=slots, slot_max_n=20000, slot_max_nnz=200000, loop=loop)
+    for name, slots, bmax in (("alone", 1, 0), ("slots", 4, 0), ("merged", 2, 8)):
+        srv = mis2.Server(slots=slots, slot_max_n=20000 * max(bmax, 1), slot_max_nnz=200000 * max(bmax, 1),
+                          batch_max=bmax, loop=loop)
         res, mif = srv.replay(host, arrivals, idx, seed=3)
         srv.close()
         assert all(r.status == 0 for r in res)
-        results[slots] = res
+        results[name] = res
         for r, gi in zip(res, idx):
             assert r.checksum == expect[gi], "result differs from the oracle"
-        if slots == 1:
+        if name == "alone":
             assert mif == 1
-    # same bits alone (1 slot) and in the mix (4 slots)
-    assert [r.checksum for r in results[1]] == [r.checksum for r in results[4]]
+    assert [r.checksum for r in results["alone"]] == [r.checksum for r in results["slots"]]
+    assert [r.checksum for r in results["alone"]] == [r.checksum for r in results["merged"]]
+
+
+def _cfg5_requests():
+    """Requests of the serving workload's sizes: a 160^3 7-point grid and
+    R-MAT scale 20 (average degree 16), plus two small ones."""
+    graphs = [gg.grid3d_7pt(160, 160, 160), gg.rmat(20, 8, seed=21, rowptr_dtype=np.int32),
+              gg.grid3d_7pt(20, 20, 20), gg.rmat(14, 8, seed=22, rowptr_dtype=np.int32)]
+    keep = [(np.ascontiguousarray(g.rowptr), np.ascontiguousarray(g.colind)) for g in graphs]
+    host = [mis2.host_csr(rp, ci, g.n) for g, (rp, ci) in zip(graphs, keep)]
+    return graphs, keep, host
+
+
+@pytest.mark.parametrize("bmax", [0, 4])
+def test_cfg5_sized_results_equal_the_oracle_element_by_element(bmax):
+    """Every output array of every request, returned through the server
+    (one request per slot, and merged launches), equals the oracle's element
+    by element, with the requests in flight together."""
+    graphs, keep, host = _cfg5_requests()
+    refs = [oracle.coarsen_level(g, seed=2) for g in graphs]
+    tot_n, tot_nnz = sum(g.n for g in graphs), sum(g.nnz for g in graphs)
+    srv = mis2.Server(slots=2, slot_max_n=tot_n if bmax else max(g.n for g in graphs),
+                      slot_max_nnz=tot_nnz if bmax else max(g.nnz for g in graphs), batch_max=bmax,
+                      mem_budget=32 << 30)
+    order = [0, 1, 2, 3, 2, 3, 1, 0]
+    subs = [(gi,) + srv.submit_out(host[gi], graphs[gi].n, graphs[gi].nnz, 2) for gi in order]
+    for gi, t, bufs in subs:
+        r = srv.wait(t)
+        ref = refs[gi]
+        assert r.status == 0
+        assert r.n_roots == len(ref.roots) and r.n_aggs == ref.n_aggs and r.c_nnz == len(ref.c_colind)
+        n = graphs[gi].n
+        assert np.array_equal(bufs["in_set"][:n], ref.in_set)
+        assert np.array_equal(bufs["roots"][:r.n_roots], ref.roots)
+        assert np.array_equal(bufs["labels"][:n], ref.labels)
+        assert np.array_equal(bufs["c_rowptr"][:r.n_aggs + 1].astype(np.int64), ref.c_rowptr)
+        assert np.array_equal(bufs["c_colind"][:r.c_nnz], ref.c_colind)
+    srv.close()
+
+
+def test_merged_launches_take_queued_requests_together():
+    """Requests queued at once are served in unions of up to batch_max: some
+    share their start time, and each union stays within the slot's capacity."""
+    graphs, keep, host = _pool()
+    n_req = 40
+    idx = np.arange(n_req) % len(graphs)
+    srv = mis2.Server(slots=1, slot_max_n=60000, slot_max_nnz=600000, batch_max=8)
+    res, mif = srv.replay(host, np.zeros(n_req), idx, seed=1)
+    srv.close()
+    assert all(r.status == 0 for r in res)
+    groups = {}
+    for r, gi in zip(res, idx):
+        groups.setdefault(r.t_start, []).append(graphs[gi])
+    assert max(len(v) for v in groups.values()) >= 2, "no launch merged two requests"
+    assert all(len(v) <= 8 and sum(g.n for g in v) <= 60000 for v in groups.values())
 
 
 def test_requests_overlap_when_they_arrive_together():
