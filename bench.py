@@ -16,6 +16,11 @@ metric is edges/s = input entries per step / step time.
 - roofline: the dominant kernel's algorithmic bytes (the per-round byte model
   applied to the worklist trace the library reports) over its CUDA-event time.
 - cpu_baseline: the CPU oracle on a bounded sample of the same workload.
+- batched_vs_plain: 512 mixed graphs coarsened recursively, batched engine
+  (autotuned) against per-graph plain launches (host and device loops).
+- other_configs: the 100x100 5-point grid and R-MAT scale 22 levels, and the
+  serving comparison (Poisson requests; serial, slots, merged launches), on
+  the same line (--no-extra-configs skips them).
 - N > 1 (torchrun): independent replicas, one per GPU (the method does not
   shard); value = all ranks' edges / max-over-ranks time.
 """
@@ -354,6 +359,14 @@ def run_ours(args):
             "mis2": {"n_roots": int(nr), "n_aggs": int(na), "c_nnz": int(cn)}}
     if not args.no_batch:
         line["batched_vs_plain"] = run_batch_compare()
+    if not args.no_extra_configs and args.workload == "27pt":
+        # the other single-graph configurations and serving, on the same line
+        line["other_configs"] = {
+            "small_5pt_100x100": level_config("small", steps=20, warmup=3, loop=args.loop),
+            "rmat_scale22": level_config("rmat", steps=5, warmup=3, loop=args.loop),
+            "serving_poisson": serve_compare(requests=4000, rate=2000.0, slots=4, batch_max=16, sat_requests=2000,
+                                             below_requests=1000, loop=args.loop),
+        }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(g, args.cpu_budget)
     print(json.dumps(line), flush=True)
@@ -361,6 +374,78 @@ def run_ours(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def level_config(name, steps=10, warmup=3, loop="device"):
+    """One more coarsening-level configuration for the bench line: the
+    workload's graph (generated here, off the clock), levels through
+    mis2_coarsen_level with input resident and L2 flushed before each, CUDA
+    events around each level; the same through mis2_coarsen_level_host (host
+    CSR in, every output out) for e2e."""
+    import torch
+
+    from paper_2204_02934_gb300 import mis2
+
+    t_gen = time.perf_counter()
+    g, desc = _workload(name)
+    t_gen = time.perf_counter() - t_gen
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lp = mis2.MIS2_LOOP_DEVICE if loop == "device" else mis2.MIS2_LOOP_HOST
+    ctx = mis2.Context(g.n, g.nnz, loop=lp, timing=1)
+    dg = mis2.DeviceGraph.from_host(g, dev)
+    n = g.n
+    bufs = [torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+            torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n + 1, dtype=torch.int32, device=dev),
+            torch.empty(g.nnz, dtype=torch.int32, device=dev)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step = lambda: mis2.mis2_coarsen_level(ctx.handle, dg.csr, 0, *bufs, g.nnz, stream)
+    for _ in range(max(warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    ms, launches = [], 0
+    kernel_ms = np.zeros(mis2.MIS2_NUM_KERNEL_CLASSES)
+    for _ in range(steps):
+        flush.fill_(1)
+        ev0.record(stream)
+        nr, na, cn = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+        st = ctx.stats()
+        launches += st.launches
+        kernel_ms += np.array(st.kernel_ms[:])
+    rounds, rounds2 = int(st.rounds), int(st.rounds2)
+    # e2e through the host-buffer entry point
+    rp_h = torch.from_numpy(np.ascontiguousarray(g.rowptr)).pin_memory()
+    ci_h = torch.from_numpy(np.ascontiguousarray(g.colind)).pin_memory()
+    outs = [torch.empty(n, dtype=torch.uint8).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory(),
+            torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n + 1, dtype=torch.int32).pin_memory(),
+            torch.empty(g.nnz, dtype=torch.int32).pin_memory()]
+    hcsr = mis2.mis2_csr(n, g.nnz, 1 if g.rowptr.dtype == np.int64 else 0, 0, rp_h.data_ptr(), ci_h.data_ptr())
+    e2e_step = lambda: mis2.mis2_coarsen_level_host(ctx.handle, hcsr, 0, *outs, g.nnz, stream)
+    for _ in range(2):
+        e2e_step()
+    e2e = []
+    for _ in range(max(2, min(steps, 5))):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e.append(time.perf_counter() - t0)
+    ctx.close()
+    tot = sum(ms) / 1e3
+    names = mis2.KERNEL_CLASSES
+    return {"workload": desc, "n": g.n, "nnz": g.nnz, "value": g.nnz * len(ms) / tot, "unit": "edges/s",
+            "ms_per_level": 1e3 * tot / len(ms), "steps": len(ms),
+            "kernel_ms_per_level": {names[k]: round(kernel_ms[k] / len(ms), 4) for k in range(len(names))
+                                    if kernel_ms[k] > 0},
+            "gpu_launches_per_level": launches // len(ms), "rounds": rounds, "rounds_phase2": rounds2,
+            "mis2": {"n_roots": int(nr), "n_aggs": int(na), "c_nnz": int(cn)},
+            "e2e": {"value": g.nnz * len(e2e) / sum(e2e), "unit": "edges/s"},
+            "generation_s": round(t_gen, 1), "l2": "flushed (256 MiB write) before every timed level"}
 
 
 def run_batch_compare(steps=3, warmup=2, n_graphs=512, seed=7, min_n=1000):
@@ -788,6 +873,8 @@ def main():
     ap.add_argument("--loop", default="device", choices=["device", "host"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the 100x100 5-point grid, R-MAT scale 22 and serving entries of the default line")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--requests", type=int, default=20000, help="serve: requests in the Poisson stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: offered requests/s")
