@@ -158,6 +158,8 @@ static void free_all(mis2_ctx* c) {
   c->h_trace = nullptr;
   for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);
   c->timer.ev.clear();
+  if (c->ev_counts) cudaEventDestroy(c->ev_counts);
+  c->ev_counts = nullptr;
 }
 
 static int alloc_scratch(mis2_ctx* c) {
@@ -485,7 +487,16 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
   MIS2_CUDA(cudaMemcpyAsync(c->h_trace, s.dtrace, 2 * MIS2_TRACE_CAP * 4 * sizeof(int64_t), cudaMemcpyDeviceToHost,
                             st));
   MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  MIS2_CUDA(cudaStreamSynchronize(st));
+  if (c->ev_counts == nullptr) MIS2_CUDA(cudaEventCreateWithFlags(&c->ev_counts, cudaEventDisableTiming));
+  MIS2_CUDA(cudaEventRecord(c->ev_counts, st));
+  // the coarse graph's labels-only steps run while the host waits for the
+  // counts (n_aggs sizes the rest)
+  bool cand_ready = false;
+  if (c_rowptr != nullptr) {
+    NvtxRange r("coarse graph");
+    MIS2_TRY(coarsen_prelude(c, ga, lab, &cand_ready, st));
+  }
+  MIS2_CUDA(cudaEventSynchronize(c->ev_counts));
   MIS2_TRY(device_error(c->h_ctr[kCtrErr]));
   const int64_t nr = c->h_ctr[kCtrRoots];
   const int64_t na = nr + c->h_ctr[kCtrQual];
@@ -501,7 +512,7 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
   int64_t cn = 0;
   if (c_rowptr != nullptr) {
     NvtxRange r("coarse graph");
-    MIS2_TRY(coarsen_fast(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, st));
+    MIS2_TRY(coarsen_fast(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, st, true, cand_ready));
     MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MIS2_CUDA(cudaStreamSynchronize(st));
     if (coarsen_fast_needs_retry(c)) {

@@ -911,7 +911,7 @@ static GraphView<I> gview_of(const GraphArgs& g) {
 // its launches.
 template <typename I>
 static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t* labels, int64_t n_aggs,
-                              bool small_on, cudaStream_t st) {
+                              bool small_on, cudaStream_t st, bool cand_ready = false) {
   Scratch& s = c->s;
   const int rows_blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
   if (small_on) {
@@ -922,14 +922,17 @@ static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t
     return MIS2_OK;
   }
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
-  k_coarse_cand<I><<<grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
+  if (!cand_ready) {
+    k_coarse_cand<I><<<grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
+    c->launches++;
+  }
   k_coarse_merge<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
                                                                           s.cand, s.tmp, s.c_cnt, s.left_mid,
                                                                           s.ctr + kCtrCoarseRest, small_on);
   k_coarse_rows<I><<<rows_blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
                                                               s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on,
                                                               s.left_mid, s.ctr + kCtrCoarseRest);
-  c->launches += 3;
+  c->launches += 2;
   return MIS2_OK;
 }
 
@@ -1044,9 +1047,46 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
 // aggregates than one batch holds set kErrLargeOverflow; the caller then
 // finishes the remaining batches (coarsen_fast_needs_retry,
 // coarsen_fast_finish).
+// The part of the fast coarse graph that needs the labels but not the
+// aggregate count, so that it can be queued before the host learns n_aggs:
+// the member counts and degree sums per aggregate (over every possible
+// aggregate id: n words) and, for graphs dense enough that the
+// candidate/merge path is likely (average degree >= kEarlyCandDegree), the
+// per-vertex candidate labels.  Returns whether the candidates were queued.
+constexpr int kEarlyCandDegree = 20;
+
+template <typename I>
+static int coarse_prelude_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready,
+                            cudaStream_t st) {
+  Scratch& s = c->s;
+  const GraphView<I> gv = gview_of<I>(g);
+  const int64_t n = g.n;
+  *cand_ready = false;
+  if (n == 0) return MIS2_OK;
+  timer_begin(c, kKcCoarse, st);
+  MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n * sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n * sizeof(int32_t), st));
+  k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
+  c->launches++;
+  if (g.nnz >= (int64_t)kEarlyCandDegree * n) {
+    k_coarse_cand<I><<<grid_for(c, (n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
+    c->launches++;
+    *cand_ready = true;
+  }
+  timer_end(c, st);
+  MIS2_CUDA(cudaGetLastError());
+  return MIS2_OK;
+}
+
+int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st) {
+  return g.rp64 ? coarse_prelude_t<int64_t>(c, g, labels, cand_ready, st)
+                : coarse_prelude_t<int32_t>(c, g, labels, cand_ready, st);
+}
+
 template <typename I>
 static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
-                          int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st) {
+                          int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done,
+                          bool cand_ready) {
   Scratch& s = c->s;
   GraphView<I> gv;
   gv.rowptr = static_cast<const I*>(g.rowptr);
@@ -1062,12 +1102,16 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
     return MIS2_OK;
   }
   timer_begin(c, kKcCoarse, st);
-  MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n_aggs * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n_aggs * sizeof(int32_t), st));
+  if (!prelude_done) {
+    MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n_aggs * sizeof(int32_t), st));
+    MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n_aggs * sizeof(int32_t), st));
+  }
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLarge, 0, 2 * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLargeKb, 0, sizeof(int32_t), st));
-  k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
-  c->launches++;
+  if (!prelude_done) {
+    k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
+    c->launches++;
+  }
   timer_end(c, st);
   MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st));
   MIS2_TRY(exclusive_scan_i32(c, s.ub, n_aggs, s.ub_ptr, nullptr, st));
@@ -1082,7 +1126,7 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
         gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
     c->launches++;
   }
-  MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st));
+  MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st, cand_ready));
   const int64_t words = (n_aggs + 31) / 32;
   const int32_t slots = bitmap_slots(c, n_aggs);
   k_large_chunks<<<1, kBlock, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
@@ -1114,9 +1158,11 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
 }
 
 int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
-                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st) {
-  return g.rp64 ? coarsen_fast_t<int64_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st)
-                : coarsen_fast_t<int32_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st);
+                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done, bool cand_ready) {
+  return g.rp64 ? coarsen_fast_t<int64_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st, prelude_done,
+                                          cand_ready)
+                : coarsen_fast_t<int32_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st, prelude_done,
+                                          cand_ready);
 }
 
 bool coarsen_fast_needs_retry(const mis2_ctx* c) { return (c->h_ctr[kCtrErr] & kErrLargeOverflow) != 0; }

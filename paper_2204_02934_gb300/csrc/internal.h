@@ -154,6 +154,7 @@ struct mis2_ctx {
   // one grid-synchronised kernel of theirs is resident at a time.
   std::mutex* coop_lock = nullptr;
   cudaEvent_t coop_done = nullptr;
+  cudaEvent_t ev_counts = nullptr;  // a level's counter readback, waited on while later work runs
   // mis2_run_snapshots: per-round copies of T and M (device; null otherwise)
   uint32_t* snaps = nullptr;
   int32_t snap_rounds = 0;
@@ -243,7 +244,11 @@ int agg_level_async(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const
 // aggregates than one batch of bitmaps: coarsen_fast_finish completes the
 // result) and kErrCapacity (c_colind too small) before trusting the result.
 int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
-                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st);
+                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done = false,
+                 bool cand_ready = false);
+// The labels-only first steps of coarsen_fast, queued before n_aggs is known
+// on the host (then pass prelude_done = true and the returned cand_ready).
+int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st);
 bool coarsen_fast_needs_retry(const mis2_ctx* c);
 // Debug-mode validation (synchronises): MIS2_ERR_BAD_GRAPH for a malformed or
 // asymmetric CSR, or for roots that are not ascending and pairwise more than
