@@ -19,32 +19,73 @@ namespace mis2 {
 constexpr int kPhase3Window = 8192;   // aggregate ids counted per pass for the heaviest rows
 constexpr int kPhase3SortCap = 8192;  // rows up to this length are sorted in shared memory
 
+// Claim the entries of row [s, e) still labelled -1 (other than v itself)
+// for aggregate id, lane lg of a group of G lanes taking 16-byte pieces.
+// The labels of a piece are all read before any is written: the vertices one
+// claim touches are distinct, and no other root's claim touches them, so the
+// reads need not wait for one another.
+template <int G>
+__device__ __forceinline__ void claim_row(const int32_t* __restrict__ colind, int64_t nnz, int64_t s, int64_t e,
+                                          int lg, bool vec, int32_t v, int32_t id, int32_t* labels) {
+  if (vec) {
+    for (int64_t p = (s & ~int64_t(3)) + 4 * lg; p < e; p += 4 * G) {
+      int32_t w[4];
+      if (p + 4 <= nnz) {
+        const int4 q = __ldg(reinterpret_cast<const int4*>(colind + p));
+        w[0] = q.x;
+        w[1] = q.y;
+        w[2] = q.z;
+        w[3] = q.w;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) w[k] = p + k < e ? __ldg(colind + p + k) : v;
+      }
+      bool in[4];
+      int32_t l[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        in[k] = p + k >= s && p + k < e && w[k] != v;
+        l[k] = in[k] ? labels[w[k]] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (in[k] && l[k] == -1) labels[w[k]] = id;
+    }
+  } else {
+    for (int64_t p = s + lg; p < e; p += G) {
+      const int32_t w = __ldg(colind + p);
+      if (w != v && labels[w] == -1) labels[w] = id;
+    }
+  }
+}
+
 // Root list entry j claims itself and every neighbour still labelled -1 for
-// aggregate base + j.  Roots are more than two hops apart (in the graph, or
-// in the phase-2 subgraph), so no two claims touch the same vertex.  Rows of
+// aggregate base + j, a group of G lanes per root (32 / G roots in flight
+// per warp).  Roots are more than two hops apart (in the graph, or in the
+// phase-2 subgraph), so no two claims touch the same vertex.  Rows of
 // degree >= block_degree are deferred to the block kernel.
-template <typename I>
+template <int G, typename I>
 __global__ void __launch_bounds__(kBlock) k_agg_claim(GraphView<I> g, const int32_t* list, int64_t n_host,
                                                       const int32_t* n_dev, int32_t* labels, int32_t base_host,
                                                       const int32_t* base_dev, int32_t* heavy, int32_t* heavy_cnt,
                                                       int32_t block_degree) {
+  constexpr int RPW = 32 / G;
   const int64_t cnt = n_dev != nullptr ? block_load(n_dev) : n_host;
   const int32_t base = base_dev != nullptr ? block_load(base_dev) : base_host;
-  const int lane = lane_id();
+  const int lane = lane_id(), lg = lane & (G - 1);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
+  for (int64_t j = warp * RPW + lane / G; j < cnt; j += nw * RPW) {
     const int32_t v = list[j];
     int64_t s, e;
     row_range(g, v, s, e);
     if (e - s >= block_degree) {
-      if (lane == 0) heavy[atomicAdd(heavy_cnt, 1)] = (int32_t)j;
+      if (lg == 0) heavy[atomicAdd(heavy_cnt, 1)] = (int32_t)j;
       continue;
     }
     const int32_t id = base + (int32_t)j;
-    if (lane == 0) labels[v] = id;
-    visit_row<32>(g.colind, g.nnz, s, e, lane, g.vec, [&](int32_t w) {
-      if (w != v && labels[w] == -1) labels[w] = id;
-    });
+    if (lg == 0) labels[v] = id;
+    claim_row<G>(g.colind, g.nnz, s, e, lg, g.vec, v, id, labels);
   }
 }
 
@@ -62,63 +103,78 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim_block(GraphView<I> g, cons
     row_range(g, v, s, e);
     const int32_t id = base + j;
     if (threadIdx.x == 0) labels[v] = id;
-    visit_row<kBlock>(g.colind, g.nnz, s, e, threadIdx.x, g.vec, [&](int32_t w) {
-      if (w != v && labels[w] == -1) labels[w] = id;
-    });
+    claim_row<kBlock>(g.colind, g.nnz, s, e, threadIdx.x, g.vec, v, id, labels);
   }
 }
 
 // Phase 2 test: qflag[v] = 1 for a phase-2 root v with >= 2 unaggregated
-// neighbours u != v (labels at the end of phase 1).  Warp per root.
-template <typename I>
+// neighbours u != v (labels at the end of phase 1).  A group of G lanes per
+// root.
+template <int G, typename I>
 __global__ void __launch_bounds__(kBlock) k_qualify(GraphView<I> g, const int32_t* list, const int32_t* n_dev,
                                                     const int32_t* labels, uint8_t* qflag) {
+  constexpr int RPW = 32 / G;
   const int64_t cnt = block_load(n_dev);
-  const int lane = lane_id();
+  const int lane = lane_id(), lg = lane & (G - 1);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < cnt; j += nw) {
-    const int32_t v = list[j];
-    int64_t s, e;
-    row_range(g, v, s, e);
+  // every lane runs the same trip count: group_sum spans the warp
+  for (int64_t jb = warp * RPW; jb < cnt; jb += nw * RPW) {
+    const int64_t j = jb + lane / G;
     int c = 0;
-    visit_row<32>(g.colind, g.nnz, s, e, lane, g.vec, [&](int32_t w) { c += (w != v && labels[w] == -1); });
-    c = group_sum<32>(c);
-    if (lane == 0) qflag[v] = c >= 2 ? 1 : 0;
+    int32_t v = -1;
+    if (j < cnt) {
+      v = list[j];
+      int64_t s, e;
+      row_range(g, v, s, e);
+      visit_row<G>(g.colind, g.nnz, s, e, lg, g.vec, [&](int32_t w) { c += (w != v && labels[w] == -1); });
+    }
+    c = group_sum<G>(c);
+    if (j < cnt && lg == 0) qflag[v] = c >= 2 ? 1 : 0;
   }
 }
 
-// aggsize(a) = |{v : tent_v = a}|, one atomic per distinct label per warp.
-__global__ void __launch_bounds__(kBlock) k_aggsize(int64_t n, const int32_t* tent, int32_t* aggsize) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+// aggsize(a) = |{v : tent_v = a}| (one atomic per distinct label per warp),
+// and the leftovers of phases 1-2 split by degree: short rows (<=
+// kLaneRowMax entries) to `left`, medium rows to `mid`, rows above
+// kPhase3SortCap to `heavy`.  The appends of a block's 256 vertices take one
+// reservation per list (one scan of the three counts packed in one word).
+// labels_out (or null): receives tent_v for every aggregated v.
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_aggsize_leftovers(GraphView<I> g, const int32_t* tent, int32_t* aggsize,
+                                                              int32_t* labels_out, int32_t* left, int32_t* left_cnt,
+                                                              int32_t* mid, int32_t* mid_cnt, int32_t* heavy,
+                                                              int32_t* heavy_cnt) {
+  __shared__ int sh_scan[40];
+  __shared__ int32_t sh_base[3];
   const int lane = lane_id();
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
-    const int64_t v = base + lane;
-    const int32_t a = v < n ? tent[v] : -1;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    const int32_t a = v < g.n ? tent[v] : -2;
     const unsigned peers = __match_any_sync(kFull, a);
     if (a >= 0 && lane == __ffs(peers) - 1) atomicAdd(aggsize + a, __popc(peers));
-  }
-}
-
-// Leftovers of phases 1-2, split by degree: short rows (<= kLaneRowMax
-// entries) to `left`, medium rows to `mid`, rows above kPhase3SortCap to
-// `heavy`.
-template <typename I>
-__global__ void __launch_bounds__(kBlock) k_leftovers(GraphView<I> g, const int32_t* tent, int32_t* left,
-                                                      int32_t* left_cnt, int32_t* mid, int32_t* mid_cnt,
-                                                      int32_t* heavy, int32_t* heavy_cnt) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int lane = lane_id();
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < g.n; base += stride) {
-    const int64_t v = base + lane;
+    if (a >= 0 && labels_out != nullptr) labels_out[v] = a;
     int cls = -1;
-    if (v < g.n && tent[v] == -1) {
+    if (a == -1) {
       int64_t s, e;
       row_range(g, v, s, e);
       cls = e - s <= kLaneRowMax ? 0 : (e - s <= kPhase3SortCap ? 1 : 2);
     }
-    warp_append(cls == 0, (int32_t)v, left, left_cnt);
-    warp_append(cls == 1, (int32_t)v, mid, mid_cnt);
-    warp_append(cls == 2, (int32_t)v, heavy, heavy_cnt);
+    // 10 bits per list: at most 256 entries of each per block
+    const int x = cls < 0 ? 0 : 1 << (10 * cls);
+    int total;
+    const int pos = block_exclusive_scan(x, sh_scan, &total);
+    if (threadIdx.x < 3) {
+      const int k = threadIdx.x, nk = (total >> (10 * k)) & 1023;
+      int32_t* ck = k == 0 ? left_cnt : (k == 1 ? mid_cnt : heavy_cnt);
+      sh_base[k] = nk > 0 ? atomicAdd(ck, nk) : 0;
+    }
+    __syncthreads();
+    if (cls >= 0) {
+      int32_t* lk = cls == 0 ? left : (cls == 1 ? mid : heavy);
+      lk[sh_base[cls] + ((pos >> (10 * cls)) & 1023)] = (int32_t)v;
+    }
+    __syncthreads();
   }
 }
 
@@ -126,9 +182,63 @@ __device__ __forceinline__ bool better(int c, int sz, int a, int bc, int bs, int
   return ba < 0 || c > bc || (c == bc && (sz < bs || (sz == bs && a < ba)));
 }
 
+// The best adjacent aggregate of one leftover from the tentative labels of
+// its W row entries (lab[k] < 0: no aggregate, or not an entry): sort them
+// in registers (a bitonic network with fixed indices), the coupling of an
+// aggregate being the length of its run; then, over the runs of maximum
+// length, the minimum size and, the runs lying in ascending label order, the
+// first of those.  The sizes of those runs only are read, and all at once.
+// Returns -1 when no entry has an aggregate.
+template <int W>
+__device__ __forceinline__ int32_t phase3_pick(int32_t (&lab)[kLaneRowMax], const int32_t* aggsize) {
+  constexpr int32_t kNone = 0x7FFFFFFF;  // sorts after every label
+#pragma unroll
+  for (int k = 0; k < W; k++) lab[k] = lab[k] < 0 ? kNone : lab[k];
+#pragma unroll
+  for (int k = 2; k <= W; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < W; i++) {
+        const int l = i ^ j;
+        if (l > i) {
+          const int32_t x = lab[i], y = lab[l];
+          const bool up = (i & k) == 0;
+          lab[i] = up ? min(x, y) : max(x, y);
+          lab[l] = up ? max(x, y) : min(x, y);
+        }
+      }
+    }
+  }
+  int cmax = 0, run = 0;
+#pragma unroll
+  for (int k = 0; k < W; k++) {
+    run = (k > 0 && lab[k] == lab[k - 1]) ? run + 1 : 1;
+    if (lab[k] != kNone) cmax = max(cmax, run);
+  }
+  if (cmax == 0) return -1;
+  int32_t sz[W];
+  run = 0;
+#pragma unroll
+  for (int k = 0; k < W; k++) {  // a run of length cmax ends at k: read its size
+    run = (k > 0 && lab[k] == lab[k - 1]) ? run + 1 : 1;
+    const bool end = lab[k] != kNone && run == cmax && (k == W - 1 || lab[k + 1] != lab[k]);
+    sz[k] = end ? __ldg(aggsize + lab[k]) : 0x7FFFFFFF;
+  }
+  int32_t best = -1, bs = 0x7FFFFFFF;
+#pragma unroll
+  for (int k = 0; k < W; k++) {
+    if (sz[k] < bs) {  // strict: equal sizes keep the smaller label, met first
+      bs = sz[k];
+      best = lab[k];
+    }
+  }
+  return best;
+}
+
 // Phase 3, one lane per short leftover row: stage the row, gather its
-// neighbours' tentative labels into the lane's own shared-memory slot, and
-// pick the best adjacent aggregate by (max coupling, min size, min id).
+// neighbours' tentative labels into registers, and pick the best adjacent
+// aggregate by (max coupling, min size, min id).
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
                                                         const int32_t* left, const int32_t* left_cnt, int32_t* labels,
@@ -149,8 +259,8 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
       row_range(g, v, s, e);
     }
     const int len = active ? (int)(e - s < kLaneRowMax ? e - s : kLaneRowMax) : -1;  // leftovers here have <= 32 entries
-    // this lane's row (staged), overwritten below with its labels
-    int32_t* myw = const_cast<int32_t*>(stage_rows_warp(g.colind, g.nnz, g.vec, s, len, area));
+    int wd;
+    const int32_t* myw = stage_rows_warp(g.colind, g.nnz, g.vec, s, len, area, &wd);
     int32_t lab[kLaneRowMax];
 #pragma unroll
     for (int j = 0; j < kLaneRowMax; j++) {
@@ -161,29 +271,10 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
       }
       lab[j] = t;
     }
-#pragma unroll
-    for (int j = 0; j < kLaneRowMax; j++)
-      if (j < len) myw[j] = lab[j];  // own row only: rows of other lanes may follow it
     int32_t best = -1;
-    int bc = 0, bs = 0;
-    for (int j = 0; j < len; j++) {
-      const int32_t a = myw[j];
-      if (a < 0) continue;
-      int c = 0, first = j;
-      for (int k = 0; k < len; k++) {
-        if (myw[k] == a) {
-          c++;
-          first = min(first, k);
-        }
-      }
-      if (first != j) continue;  // counted at its first occurrence
-      const int sz = aggsize[a];
-      if (better(c, sz, a, bc, bs, best)) {
-        best = a;
-        bc = c;
-        bs = sz;
-      }
-    }
+    if (wd == 8) best = phase3_pick<8>(lab, aggsize);
+    else if (wd == 16) best = phase3_pick<16>(lab, aggsize);
+    else best = phase3_pick<32>(lab, aggsize);
     if (active) {
       labels[v] = best;
       if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
@@ -348,19 +439,69 @@ static GraphView<I> gview(const GraphArgs& g) {
   return v;
 }
 
+// Lanes per root row for the claim and qualify kernels: 4 entries per lane
+// and pass, so that a row of average length takes one pass.
+static int root_lanes(int64_t n, int64_t nnz) {
+  const int64_t avg = nnz / std::max<int64_t>(n, 1) + 3;
+  return avg <= 16 ? 4 : (avg <= 32 ? 8 : (avg <= 64 ? 16 : 32));
+}
+
+template <int G, typename I>
+static void launch_claim_g(mis2_ctx* c, const GraphView<I>& gv, const int32_t* list, int64_t n_host,
+                           const int32_t* n_dev, int32_t* labels, int32_t base, cudaStream_t st,
+                           const int32_t* base_dev, int32_t* heavy_cnt) {
+  Scratch& s = c->s;
+  const int64_t items = n_dev != nullptr ? gv.n : n_host;
+  k_agg_claim<G, I><<<grid_for(c, items, kBlock / G), kBlock, 0, st>>>(gv, list, n_host, n_dev, labels, base,
+                                                                        base_dev, s.left_heavy, heavy_cnt,
+                                                                        c->cfg.block_degree);
+  k_agg_claim_block<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, list, s.left_heavy, heavy_cnt, labels, base,
+                                                           base_dev);
+  c->launches += 2;
+}
+
+// heavy_cnt: the deferred-row counter, zero on entry (null: the context's,
+// cleared here)
 template <typename I>
 static void launch_claim(mis2_ctx* c, const GraphView<I>& gv, const int32_t* list, int64_t n_host,
                          const int32_t* n_dev, int32_t* labels, int32_t base, cudaStream_t st,
-                         const int32_t* base_dev = nullptr) {
+                         const int32_t* base_dev = nullptr, int32_t* heavy_cnt = nullptr) {
+  if (heavy_cnt == nullptr) {
+    heavy_cnt = c->s.ctr + kCtrHeavy;
+    cudaMemsetAsync(heavy_cnt, 0, sizeof(int32_t), st);
+  }
+  switch (root_lanes(gv.n, gv.nnz)) {
+    case 4: launch_claim_g<4, I>(c, gv, list, n_host, n_dev, labels, base, st, base_dev, heavy_cnt); break;
+    case 8: launch_claim_g<8, I>(c, gv, list, n_host, n_dev, labels, base, st, base_dev, heavy_cnt); break;
+    case 16: launch_claim_g<16, I>(c, gv, list, n_host, n_dev, labels, base, st, base_dev, heavy_cnt); break;
+    default: launch_claim_g<32, I>(c, gv, list, n_host, n_dev, labels, base, st, base_dev, heavy_cnt); break;
+  }
+}
+
+template <typename I>
+static void launch_qualify(mis2_ctx* c, const GraphView<I>& gv, const int32_t* list, const int32_t* n_dev,
+                           const int32_t* labels, uint8_t* qflag, cudaStream_t st) {
+  const int G = root_lanes(gv.n, gv.nnz);
+  const int grid = grid_for(c, gv.n, kBlock / G);
+  switch (G) {
+    case 4: k_qualify<4, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
+    case 8: k_qualify<8, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
+    case 16: k_qualify<16, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
+    default: k_qualify<32, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
+  }
+  c->launches++;
+}
+
+// labels_out: where the aggregated vertices' labels are copied (null: they
+// are there already)
+template <typename I>
+static void launch_leftovers(mis2_ctx* c, const GraphView<I>& gv, cudaStream_t st, int32_t* labels_out = nullptr) {
   Scratch& s = c->s;
-  const int64_t items = n_dev != nullptr ? gv.n : n_host;
-  cudaMemsetAsync(s.ctr + kCtrHeavy, 0, sizeof(int32_t), st);
-  k_agg_claim<I><<<grid_for(c, items, kBlock / 32), kBlock, 0, st>>>(gv, list, n_host, n_dev, labels, base,
-                                                                      base_dev, s.left_heavy, s.ctr + kCtrHeavy,
-                                                                      c->cfg.block_degree);
-  k_agg_claim_block<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, list, s.left_heavy, s.ctr + kCtrHeavy, labels,
-                                                           base, base_dev);
-  c->launches += 2;
+  k_aggsize_leftovers<I><<<grid_for(c, gv.n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.aggsize, labels_out, s.left,
+                                                                        s.ctr + kCtrLeft, s.left_mid,
+                                                                        s.ctr + kCtrLeftMid, s.left_heavy,
+                                                                        s.ctr + kCtrLeftHeavy);
+  c->launches++;
 }
 
 template <typename I>
@@ -403,8 +544,7 @@ static int phase2_t(mis2_ctx* c, const GraphArgs& g, const PrioCfg& p, int32_t* 
   MIS2_TRY(extract_in_set(c, n, nullptr, s.roots2, s.ctr + kCtrM2, st));
   MIS2_CUDA(cudaMemsetAsync(s.qflag, 0, n, st));
   timer_begin(c, kKcAggregate, st);
-  k_qualify<I><<<grid_for(c, n, kBlock / 32), kBlock, 0, st>>>(gv, s.roots2, s.ctr + kCtrM2, labels, s.qflag);
-  c->launches++;
+  launch_qualify<I>(c, gv, s.roots2, s.ctr + kCtrM2, labels, s.qflag, st);
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   MIS2_TRY(compact_flags(c, s.qflag, nullptr, n, s.qlist, s.ctr + kCtrQual, st));
@@ -429,10 +569,7 @@ static int phase3_t(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t to
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeft, 0, 2 * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrErr, 0, sizeof(int32_t), st));
-  k_aggsize<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, s.tent, s.aggsize);
-  k_leftovers<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.left, s.ctr + kCtrLeft, s.left_mid,
-                                                             s.ctr + kCtrLeftMid, s.left_heavy, s.ctr + kCtrLeftHeavy);
-  c->launches += 2;
+  launch_leftovers<I>(c, gv, st);
   launch_phase3<I>(c, gv, labels, st);
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
@@ -458,40 +595,38 @@ int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, 
   return g.rp64 ? phase3_t<int64_t>(c, g, labels, total, st) : phase3_t<int32_t>(c, g, labels, total, st);
 }
 
+// The level's aggregation without host synchronisation.  The counter words
+// it uses were cleared at the level's start.  Phases 1 and 2 label into
+// s.tent, the frozen labels phase 3 reads; the fused sizes / leftovers pass
+// copies every aggregated vertex's label to `labels`, and phase 3 adds the
+// leftovers' (no device-to-device copy of the labels).
 template <typename I>
 static int agg_async_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const PrioCfg& p, int mode,
                        int32_t* labels, cudaStream_t st) {
   Scratch& s = c->s;
   const GraphView<I> gv = gview<I>(g);
   const int64_t n = g.n;
-  MIS2_CUDA(cudaMemsetAsync(labels, 0xFF, n * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrM2, 0, (kCtrLeftHeavy - kCtrM2 + 1) * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
+  int32_t* tent = s.tent;
+  MIS2_CUDA(cudaMemsetAsync(tent, 0xFF, n * sizeof(int32_t), st));
   timer_begin(c, kKcAggregate, st);
-  launch_claim<I>(c, gv, roots, 0, s.ctr + kCtrRoots, labels, 0, st);
+  launch_claim<I>(c, gv, roots, 0, s.ctr + kCtrRoots, tent, 0, st, nullptr, s.ctr + kCtrHeavy);
   timer_end(c, st);
   if (mode == MIS2_AGG_ALG3) {
-    MIS2_TRY(mis2_rounds_device_async(c, g, labels, p, 1, kCtrRounds2, st));
-    MIS2_TRY(extract_in_set(c, n, nullptr, s.roots2, s.ctr + kCtrM2, st));
-    MIS2_CUDA(cudaMemsetAsync(s.qflag, 0, n, st));
+    MIS2_TRY(mis2_rounds_device_async(c, g, tent, p, 1, kCtrRounds2, st));
+    // qflag = 1 at the phase-2 roots, 0 elsewhere; k_qualify clears the
+    // roots that do not qualify
+    MIS2_TRY(extract_in_set(c, n, s.qflag, s.roots2, s.ctr + kCtrM2, st));
     timer_begin(c, kKcAggregate, st);
-    k_qualify<I><<<grid_for(c, n, kBlock / 32), kBlock, 0, st>>>(gv, s.roots2, s.ctr + kCtrM2, labels, s.qflag);
-    c->launches++;
+    launch_qualify<I>(c, gv, s.roots2, s.ctr + kCtrM2, tent, s.qflag, st);
     timer_end(c, st);
     MIS2_TRY(compact_flags(c, s.qflag, nullptr, n, s.qlist, s.ctr + kCtrQual, st));
     timer_begin(c, kKcAggregate, st);
-    launch_claim<I>(c, gv, s.qlist, 0, s.ctr + kCtrQual, labels, 0, st, s.ctr + kCtrRoots);
+    launch_claim<I>(c, gv, s.qlist, 0, s.ctr + kCtrQual, tent, 0, st, s.ctr + kCtrRoots, s.ctr + kCtrHeavy2);
     timer_end(c, st);
   }
   timer_begin(c, kKcAggregate, st);
-  MIS2_CUDA(cudaMemcpyAsync(s.tent, labels, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   MIS2_CUDA(cudaMemsetAsync(s.aggsize, 0, n * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeft, 0, 2 * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
-  k_aggsize<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, s.tent, s.aggsize);
-  k_leftovers<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.left, s.ctr + kCtrLeft, s.left_mid,
-                                                             s.ctr + kCtrLeftMid, s.left_heavy, s.ctr + kCtrLeftHeavy);
-  c->launches += 2;
+  launch_leftovers<I>(c, gv, st, labels);
   launch_phase3<I>(c, gv, labels, st);
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());

@@ -512,7 +512,7 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
   int64_t cn = 0;
   if (c_rowptr != nullptr) {
     NvtxRange r("coarse graph");
-    MIS2_TRY(coarsen_fast(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, st, true, cand_ready));
+    MIS2_TRY(coarsen_fast(c, ga, lab, na, c_rowptr, c_colind, c_colind_cap, st, true, cand_ready, true));
     MIS2_CUDA(cudaMemcpyAsync(c->h_ctr, s.ctr, kReadbackWords * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     MIS2_CUDA(cudaStreamSynchronize(st));
     if (coarsen_fast_needs_retry(c)) {

@@ -911,7 +911,7 @@ static GraphView<I> gview_of(const GraphArgs& g) {
 // its launches.
 template <typename I>
 static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t* labels, int64_t n_aggs,
-                              bool small_on, cudaStream_t st, bool cand_ready = false) {
+                              bool small_on, cudaStream_t st, bool cand_ready = false, bool ctr_fresh = false) {
   Scratch& s = c->s;
   const int rows_blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
   if (small_on) {
@@ -921,7 +921,7 @@ static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t
     c->launches++;
     return MIS2_OK;
   }
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
+  if (!ctr_fresh) MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
   if (!cand_ready) {
     k_coarse_cand<I><<<grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
     c->launches++;
@@ -1086,7 +1086,7 @@ int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool
 template <typename I>
 static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                           int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done,
-                          bool cand_ready) {
+                          bool cand_ready, bool ctr_fresh) {
   Scratch& s = c->s;
   GraphView<I> gv;
   gv.rowptr = static_cast<const I*>(g.rowptr);
@@ -1096,7 +1096,7 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   gv.vec = g.vec ? 1 : 0;
   gv.pad = 0;
   const int64_t n = g.n;
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCnnz, 0, sizeof(int32_t), st));
+  if (!ctr_fresh) MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCnnz, 0, sizeof(int32_t), st));
   if (n_aggs == 0) {
     MIS2_CUDA(cudaMemsetAsync(c_rowptr, 0, sizeof(int32_t), st));
     return MIS2_OK;
@@ -1106,8 +1106,10 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
     MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n_aggs * sizeof(int32_t), st));
     MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n_aggs * sizeof(int32_t), st));
   }
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLarge, 0, 2 * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLargeKb, 0, sizeof(int32_t), st));
+  if (!ctr_fresh) {
+    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLarge, 0, 2 * sizeof(int32_t), st));
+    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLargeKb, 0, sizeof(int32_t), st));
+  }
   if (!prelude_done) {
     k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
     c->launches++;
@@ -1126,7 +1128,7 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
         gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
     c->launches++;
   }
-  MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st, cand_ready));
+  MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st, cand_ready, ctr_fresh));
   const int64_t words = (n_aggs + 31) / 32;
   const int32_t slots = bitmap_slots(c, n_aggs);
   k_large_chunks<<<1, kBlock, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
@@ -1158,11 +1160,12 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
 }
 
 int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
-                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done, bool cand_ready) {
+                 int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done, bool cand_ready,
+                 bool ctr_fresh) {
   return g.rp64 ? coarsen_fast_t<int64_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st, prelude_done,
-                                          cand_ready)
+                                          cand_ready, ctr_fresh)
                 : coarsen_fast_t<int32_t>(c, g, labels, n_aggs, c_rowptr, c_colind, c_colind_cap, st, prelude_done,
-                                          cand_ready);
+                                          cand_ready, ctr_fresh);
 }
 
 bool coarsen_fast_needs_retry(const mis2_ctx* c) { return (c->h_ctr[kCtrErr] & kErrLargeOverflow) != 0; }

@@ -5,6 +5,12 @@
 // round.  Every barrier wait is bounded: after spin_limit polls a block
 // raises the timeout flag, all blocks leave, and the host reports
 // MIS2_ERR_TIMEOUT instead of hanging.
+//
+// A launch leaves the counter words as the next launch needs them, so that
+// back-to-back MIS-2 launches of a level need no clearing in between: the
+// worklist sizes zero, the barrier's arrival count at its value with the
+// base word (kCtrBarrier + 1) equal to it, and its trace rows zero from the
+// round where it stopped on (each round clears the next round's row).
 #include <algorithm>
 
 #include "grid_sync.cuh"
@@ -63,13 +69,18 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
 
   int64_t* ts = a.ts;
   if (ts != nullptr && tid == 0) ts[0] = global_ns();  // block 0 starts
+  // arrival count when the launch started: written by the previous launch
+  // after its last barrier, read here before this launch's first one
+  const uint32_t bar_base = (uint32_t)ld_volatile_i32(ctr + kCtrBarrier + 1);
+  if (tid == 0 && a.dtr != nullptr)
+    for (int k = 0; k < 4; k++) a.dtr[k] = 0;  // round 0's trace row
   // worklist 2 starts equal to worklist 1: round 0's column step reads the
   // worklist-1 lists, so only worklist 2's sizes are set here
   const RowLists none{{nullptr, nullptr, nullptr}};
   mis_init_rows<I>(g, a.labels, p, a.T, a.M, a.wl1[0], none, ctr + ctr_c1(0, 0), ctr + ctr_c2(0, 0),
                    a.warp_degree, a.block_degree);
   if (ts != nullptr && tid == 0) ts[1] = global_ns();  // block 0 has set up its vertices
-  if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr, a.barrier_extra)) return;
+  if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts ? ts + 2 : nullptr, a.barrier_extra, bar_base)) return;
 
   constexpr bool nowl = NOWL;
   int r = 0;
@@ -119,6 +130,8 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     // ---- column step
     if (tid < kClasses) ctr[ctr_c1(nslot, (int)tid)] = 0;
     if (tid == 0 && tr_on) a.dtr[r * 4 + 1] = w2;
+    if (tid == 0 && a.dtr != nullptr && r + 1 < MIS2_TRACE_CAP)
+      for (int k = 0; k < 4; k++) a.dtr[(r + 1) * 4 + k] = 0;  // summed into during round r + 1
     if constexpr (G == 1)
       column_lane_rows<I, false>(g, a.T, a.M, in2.l[0], n2[0], out2.l[0], ctr + ctr_c2(nslot, 0), d2, warp, nwarps,
                                  my_stage);
@@ -132,7 +145,9 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
       column_block_rows<I, false>(g, a.T, a.M, in2.l[2], n2[2], out2.l[2], ctr + ctr_c2(nslot, 2), d2, blockIdx.x,
                                   gridDim.x, sh);
     const bool ts_on = ts != nullptr && r < MIS2_TRACE_CAP;
-    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr, a.barrier_extra)) return;
+    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 4 + 4 * r : nullptr, a.barrier_extra,
+                      bar_base))
+      return;
     if (a.snaps != nullptr && r < a.snap_rounds) grid_copy(a.snaps + ((int64_t)r * 3 + 1) * g.n, a.M, g.n);
     // ---- decide step (with the next round's row refresh)
     if (tid < kClasses) ctr[ctr_c2(zslot, (int)tid)] = 0;
@@ -149,9 +164,22 @@ __global__ void __launch_bounds__(kBlock, MIS2_LOOP_MINB) k_mis_loop(GraphView<I
     if (n1[2] > 0)
       decide_block_rows<I, false, NOWL>(g, a.T, a.M, in1.l[2], n1[2], out1.l[2], ctr + ctr_c1(nslot, 2), d1, p,
                                   (uint32_t)(r + 1), blockIdx.x, gridDim.x, sh);
-    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr, a.barrier_extra)) return;
+    if (!grid_barrier(bar_count, epoch, err, a.spin_limit, ts_on ? ts + 6 + 4 * r : nullptr, a.barrier_extra,
+                      bar_base))
+      return;
   }
-  if (tid == 0) ctr[a.rounds_slot] = r;
+  // Every block has passed the last barrier, so every block has read the
+  // base and no block writes a worklist size again; a block still to read
+  // this round's sizes sees worklist 1 empty, as it is, and stops too.
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < 18) ctr[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+      ctr[a.rounds_slot] = r;
+      ctr[kCtrBarrier + 1] = (int32_t)(bar_base + (uint32_t)epoch * gridDim.x);
+      if (a.dtr != nullptr)
+        for (int k = r * 4; k < MIS2_TRACE_CAP * 4; k++) a.dtr[k] = 0;  // rows of rounds that did not run
+    }
+  }
 }
 
 template <int G, typename I>
@@ -208,15 +236,10 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.no_worklists = (c->cfg.ablation & MIS2_ABLATE_NO_WORKLISTS) ? 1 : 0;
   la.snaps = labels == nullptr ? c->snaps : nullptr;
   la.snap_rounds = c->snap_rounds;
-  if (sync) {
-    MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
-  } else {
-    // worklist counters and the barrier words only: other counters of the
-    // level (roots, errors) stay
-    MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, 18 * sizeof(int32_t), st));
-    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrBarrier, 0, 2 * sizeof(int32_t), st));
-  }
-  MIS2_CUDA(cudaMemsetAsync(la.dtr, 0, MIS2_TRACE_CAP * 4 * sizeof(int64_t), st));
+  // async: the counter words were cleared at the level's start, or left
+  // ready by the level's previous loop launch (see the top of this file);
+  // the other counters of the level (roots, errors) stay
+  if (sync) MIS2_CUDA(cudaMemsetAsync(s.ctr, 0, kCtrWords * sizeof(int32_t), st));
   if (la.ts != nullptr) MIS2_CUDA(cudaMemsetAsync(la.ts, 0, kLoopTsWords * sizeof(int64_t), st));
   timer_begin(c, kKcDeviceLoop, st);
   int rc;

@@ -22,16 +22,18 @@ __device__ __forceinline__ int64_t global_ns() {
   return (int64_t)t;
 }
 
-// Grid barrier on a monotonic arrival counter (zeroed before the launch):
-// the k-th barrier of a launch (epoch k, counted by every block) completes
-// when the counter reaches k * gridDim.x.  Each block adds 1 after a fence
-// and polls with acquire loads; there is no reset step on the critical path.
+// Grid barrier on a monotonic arrival counter: the k-th barrier of a launch
+// (epoch k, counted by every block) completes when the counter reaches
+// base + k * gridDim.x, base being the counter's value when the launch
+// started (0 after a reset; the caller passes it, since blocks that start
+// late cannot read it from the counter).  Each block adds 1 after a fence and polls with
+// acquire loads; there is no reset step on the critical path.
 // Returns false (in every thread of the block) when this block gave up
 // waiting or another block already reported a timeout.
 // ts (optional): ts[0] = latest arrival time, ts[1] = block 0's departure
 // time (globaltimer, ns).
 __device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t& epoch, int32_t* err, int64_t spin_limit,
-                                             int64_t* ts = nullptr, int32_t extra = 0) {
+                                             int64_t* ts = nullptr, int32_t extra = 0, uint32_t base = 0u) {
   __shared__ int ok;
   __syncthreads();
   epoch++;
@@ -40,7 +42,7 @@ __device__ __forceinline__ bool grid_barrier(int32_t* count, int32_t& epoch, int
     if (ts != nullptr) atomicMax(reinterpret_cast<unsigned long long*>(ts), (unsigned long long)global_ns());
     __threadfence();
     atomicAdd(count, 1);
-    const uint32_t target = (uint32_t)epoch * gridDim.x + (uint32_t)extra;
+    const uint32_t target = base + (uint32_t)epoch * gridDim.x + (uint32_t)extra;
     int64_t spins = 0;
     while ((int32_t)((uint32_t)ld_acquire_i32(count) - target) < 0) {
       if (++spins > spin_limit || (ld_volatile_i32(err) & kErrTimeout)) {

@@ -40,8 +40,9 @@ enum : int {
   kCtrCnnz = 25,     // coarse nnz
   kCtrErr = 26,      // device error flags (bit 0: barrier timeout)
   kCtrRounds = 27,   // rounds of the device loop
-  kCtrBarrier = 28,  // grid barrier: monotonic arrival count (28; 29 unused)
+  kCtrBarrier = 28,  // grid barrier: monotonic arrival count (28) and its value at the launch's start (29)
   kCtrLeftMid = 30,  // phase-3 leftovers of medium degree
+  kCtrHeavy2 = 31,   // deferred heavy rows of the phase-2 claims (async level path)
   kCtrRounds2 = 32,  // rounds of the phase-2 device loop
   kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch
   kCtrGiant = 34,    // giant member rows of the current bitmap batch
@@ -243,9 +244,11 @@ int agg_level_async(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const
 // the counters into c->h_ctr and checks coarsen_fast_needs_retry (more large
 // aggregates than one batch of bitmaps: coarsen_fast_finish completes the
 // result) and kErrCapacity (c_colind too small) before trusting the result.
+// ctr_fresh: the coarse graph's counter words are still zero from the
+// level's start (not cleared again here).
 int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t n_aggs, int32_t* c_rowptr,
                  int32_t* c_colind, int64_t c_colind_cap, cudaStream_t st, bool prelude_done = false,
-                 bool cand_ready = false);
+                 bool cand_ready = false, bool ctr_fresh = false);
 // The labels-only first steps of coarsen_fast, queued before n_aggs is known
 // on the host (then pass prelude_done = true and the returned cand_ready).
 int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st);

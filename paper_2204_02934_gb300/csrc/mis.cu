@@ -386,11 +386,12 @@ int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32
   const int64_t nt = scan_tiles(n);
   const int blocks = grid_for(c, nt, 1, 8);
   timer_begin(c, kKcCompact, st);
+  const bool direct = nt <= kScanDirectTiles;
   k_tile_count<PredIn><<<blocks, kBlock, 0, st>>>(n, PredIn{c->s.T}, c->s.tile);
-  k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, count_dev);
+  if (!direct) k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, count_dev);
   k_tile_compact<PredIn, EmitRoots><<<blocks, kBlock, 0, st>>>(n, PredIn{c->s.T}, c->s.tile,
-                                                               EmitRoots{roots, flags});
-  c->launches += 3;
+                                                               EmitRoots{roots, flags}, direct, count_dev);
+  c->launches += direct ? 2 : 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   return MIS2_OK;
@@ -405,11 +406,12 @@ int compact_flags(mis2_ctx* c, const uint8_t* flags, const int32_t* map, int64_t
   const int64_t nt = scan_tiles(n);
   const int blocks = grid_for(c, nt, 1, 8);
   timer_begin(c, kKcCompact, st);
+  const bool direct = nt <= kScanDirectTiles;
   k_tile_count<PredFlag><<<blocks, kBlock, 0, st>>>(n, PredFlag{flags}, c->s.tile);
-  k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, count_dev);
+  if (!direct) k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, count_dev);
   k_tile_compact<PredFlag, EmitMapped><<<blocks, kBlock, 0, st>>>(n, PredFlag{flags}, c->s.tile,
-                                                                  EmitMapped{map, out});
-  c->launches += 3;
+                                                                  EmitMapped{map, out}, direct, count_dev);
+  c->launches += direct ? 2 : 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   return MIS2_OK;
@@ -425,10 +427,11 @@ int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out
   const int64_t nt = scan_tiles(n);
   const int blocks = grid_for(c, nt, 1, 8);
   timer_begin(c, kKcCompact, st);
+  const bool direct = nt <= kScanDirectTiles;
   k_tile_sum<ValArr><<<blocks, kBlock, 0, st>>>(n, ValArr{vals}, c->s.tile);
-  k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, total_dev);
-  k_tile_scan_write<ValArr, int32_t><<<blocks, kBlock, 0, st>>>(n, ValArr{vals}, c->s.tile, out);
-  c->launches += 3;
+  if (!direct) k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, total_dev);
+  k_tile_scan_write<ValArr, int32_t><<<blocks, kBlock, 0, st>>>(n, ValArr{vals}, c->s.tile, out, direct, total_dev);
+  c->launches += direct ? 2 : 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   return MIS2_OK;
