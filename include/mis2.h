@@ -96,10 +96,12 @@ typedef struct {
   int32_t loop;           /* MIS2_LOOP_*; default HOST (DEVICE: one persistent launch per MIS-2 or
                              colouring) */
   int32_t debug_checks;   /* MIS2_DEBUG_* bits (extra passes, synchronising); default 0 */
-  int32_t timing;         /* record per-kernel CUDA-event times into mis2_stats; default 0 */
+  int32_t timing;         /* MIS2_TIMING_*: CUDA-event times per kernel class into mis2_stats; default 0 */
   int32_t loop_blocks_per_sm; /* blocks per SM of the device-loop kernel: 0 = default (2) */
   int32_t ablation;       /* MIS2_ABLATE_* bits (the Fig. 2 variants); default 0 */
-  int32_t reserved;       /* 0 */
+  int32_t serial_launches; /* 1: every kernel around the MIS-2 loops is scheduled only after the
+                              previous one has finished; 0 (default): programmatic dependent
+                              launch lets it be scheduled while that one finishes (same results) */
   int64_t spin_limit;     /* polls before a device barrier reports MIS2_ERR_TIMEOUT */
 } mis2_config;
 
@@ -141,6 +143,17 @@ typedef struct {
 #define MIS2_ABLATE_TUPLE_ENGINE 0x2
 #define MIS2_ABLATE_UNPACKED_TUPLES 0x4
 
+/* timing values.
+ * MIS2_TIMING_ALL: every kernel class is bracketed by CUDA events, the
+ *   device loop stamps every grid barrier (loop_ns), and the kernels are
+ *   launched one after another (serial_launches implied), so that each
+ *   class's time is its own.
+ * MIS2_TIMING_LOOP: only the device-loop MIS-2 launches (class 6) are
+ *   bracketed by events; everything else runs as with timing off. */
+#define MIS2_TIMING_OFF 0
+#define MIS2_TIMING_ALL 1
+#define MIS2_TIMING_LOOP 2
+
 #define MIS2_DEBUG_VALIDATE 0x1
 #define MIS2_DEBUG_FORCE_TIMEOUT 0x100
 
@@ -156,13 +169,14 @@ typedef struct {
   int64_t c_nnz;            /* coarse graph entries */
   int64_t trace[MIS2_TRACE_CAP][4];
   int64_t trace2[MIS2_TRACE_CAP][4];
-  /* timing (config.timing != 0): total ms and launches per kernel class:
+  /* timing (config.timing != 0; MIS2_TIMING_LOOP: class 6 only): total ms
+   * and launches per kernel class:
    * 0 init, 1 column, 2 decide, 3 roots/compaction, 4 aggregation,
    * 5 coarse graph, 6 device-loop MIS-2 kernel, 7 other */
   double kernel_ms[MIS2_NUM_KERNEL_CLASSES];
   int64_t kernel_launches[MIS2_NUM_KERNEL_CLASSES];
   int64_t launches;         /* CUDA kernels launched by the last call (always counted) */
-  /* device loop with timing: globaltimer ns of [0] block 0's start and [1]
+  /* device loop with MIS2_TIMING_ALL: globaltimer ns of [0] block 0's start and [1]
    * the end of its round-0 set-up, then per
    * grid barrier b (b = 0 after set-up, 2r+1 after round r's column step,
    * 2r+2 after its decide step) the last block's arrival [2+2b] and block 0's

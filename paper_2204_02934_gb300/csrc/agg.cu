@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim(GraphView<I> g, const int3
                                                       const int32_t* n_dev, int32_t* labels, int32_t base_host,
                                                       const int32_t* base_dev, int32_t* heavy, int32_t* heavy_cnt,
                                                       int32_t block_degree) {
+  pdl_enter();
   constexpr int RPW = 32 / G;
   const int64_t cnt = n_dev != nullptr ? block_load(n_dev) : n_host;
   const int32_t base = base_dev != nullptr ? block_load(base_dev) : base_host;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim_block(GraphView<I> g, cons
                                                             const int32_t* heavy, const int32_t* heavy_cnt,
                                                             int32_t* labels, int32_t base_host,
                                                             const int32_t* base_dev) {
+  pdl_enter();
   const int64_t cnt = block_load(heavy_cnt);
   const int32_t base = base_dev != nullptr ? *base_dev : base_host;
   for (int64_t h = blockIdx.x; h < cnt; h += gridDim.x) {
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_agg_claim_block(GraphView<I> g, cons
 template <int G, typename I>
 __global__ void __launch_bounds__(kBlock) k_qualify(GraphView<I> g, const int32_t* list, const int32_t* n_dev,
                                                     const int32_t* labels, uint8_t* qflag) {
+  pdl_enter();
   constexpr int RPW = 32 / G;
   const int64_t cnt = block_load(n_dev);
   const int lane = lane_id(), lg = lane & (G - 1);
@@ -145,6 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_aggsize_leftovers(GraphView<I> g, co
                                                               int32_t* labels_out, int32_t* left, int32_t* left_cnt,
                                                               int32_t* mid, int32_t* mid_cnt, int32_t* heavy,
                                                               int32_t* heavy_cnt) {
+  pdl_enter();
   __shared__ int sh_scan[40];
   __shared__ int32_t sh_base[3];
   const int lane = lane_id();
@@ -243,6 +247,7 @@ template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
                                                         const int32_t* left, const int32_t* left_cnt, int32_t* labels,
                                                         int32_t* err) {
+  pdl_enter();
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   const int lane = lane_id();
   int32_t* area = stage[threadIdx.x >> 5];
@@ -289,6 +294,7 @@ template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_sort(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
                                                         const int32_t* list, const int32_t* list_cnt, int32_t* labels,
                                                         int32_t* err) {
+  pdl_enter();
   __shared__ int32_t buf[kPhase3SortCap];
   __shared__ uint32_t sh[40];
   __shared__ int fill;
@@ -363,6 +369,7 @@ template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_block(GraphView<I> g, const int32_t* tent,
                                                          const int32_t* aggsize, const int32_t* list,
                                                          const int32_t* list_cnt, int32_t* labels, int32_t* err) {
+  pdl_enter();
   __shared__ int cnt[kPhase3Window];
   __shared__ uint32_t sh[40];
   const int64_t n_items = block_load(list_cnt);
@@ -452,10 +459,10 @@ static void launch_claim_g(mis2_ctx* c, const GraphView<I>& gv, const int32_t* l
                            const int32_t* base_dev, int32_t* heavy_cnt) {
   Scratch& s = c->s;
   const int64_t items = n_dev != nullptr ? gv.n : n_host;
-  k_agg_claim<G, I><<<grid_for(c, items, kBlock / G), kBlock, 0, st>>>(gv, list, n_host, n_dev, labels, base,
+  launch_k(c, k_agg_claim<G, I>, grid_for(c, items, kBlock / G), kBlock, st, gv, list, n_host, n_dev, labels, base,
                                                                         base_dev, s.left_heavy, heavy_cnt,
                                                                         c->cfg.block_degree);
-  k_agg_claim_block<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, list, s.left_heavy, heavy_cnt, labels, base,
+  launch_k(c, k_agg_claim_block<I>, c->sm_count * 2, kBlock, st, gv, list, s.left_heavy, heavy_cnt, labels, base,
                                                            base_dev);
   c->launches += 2;
 }
@@ -484,10 +491,10 @@ static void launch_qualify(mis2_ctx* c, const GraphView<I>& gv, const int32_t* l
   const int G = root_lanes(gv.n, gv.nnz);
   const int grid = grid_for(c, gv.n, kBlock / G);
   switch (G) {
-    case 4: k_qualify<4, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
-    case 8: k_qualify<8, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
-    case 16: k_qualify<16, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
-    default: k_qualify<32, I><<<grid, kBlock, 0, st>>>(gv, list, n_dev, labels, qflag); break;
+    case 4: launch_k(c, k_qualify<4, I>, grid, kBlock, st, gv, list, n_dev, labels, qflag); break;
+    case 8: launch_k(c, k_qualify<8, I>, grid, kBlock, st, gv, list, n_dev, labels, qflag); break;
+    case 16: launch_k(c, k_qualify<16, I>, grid, kBlock, st, gv, list, n_dev, labels, qflag); break;
+    default: launch_k(c, k_qualify<32, I>, grid, kBlock, st, gv, list, n_dev, labels, qflag); break;
   }
   c->launches++;
 }
@@ -497,7 +504,7 @@ static void launch_qualify(mis2_ctx* c, const GraphView<I>& gv, const int32_t* l
 template <typename I>
 static void launch_leftovers(mis2_ctx* c, const GraphView<I>& gv, cudaStream_t st, int32_t* labels_out = nullptr) {
   Scratch& s = c->s;
-  k_aggsize_leftovers<I><<<grid_for(c, gv.n, kBlock), kBlock, 0, st>>>(gv, s.tent, s.aggsize, labels_out, s.left,
+  launch_k(c, k_aggsize_leftovers<I>, grid_for(c, gv.n, kBlock), kBlock, st, gv, s.tent, s.aggsize, labels_out, s.left,
                                                                         s.ctr + kCtrLeft, s.left_mid,
                                                                         s.ctr + kCtrLeftMid, s.left_heavy,
                                                                         s.ctr + kCtrLeftHeavy);
@@ -507,11 +514,11 @@ static void launch_leftovers(mis2_ctx* c, const GraphView<I>& gv, cudaStream_t s
 template <typename I>
 static void launch_phase3(mis2_ctx* c, const GraphView<I>& gv, int32_t* labels, cudaStream_t st) {
   Scratch& s = c->s;
-  k_phase3_lane<I><<<grid_for(c, gv.n, kBlock, 8), kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left, s.ctr + kCtrLeft,
+  launch_k(c, k_phase3_lane<I>, grid_for(c, gv.n, kBlock, 8), kBlock, st, gv, s.tent, s.aggsize, s.left, s.ctr + kCtrLeft,
                                                                      labels, s.ctr + kCtrErr);
-  k_phase3_sort<I><<<c->sm_count * 4, kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left_mid, s.ctr + kCtrLeftMid,
+  launch_k(c, k_phase3_sort<I>, c->sm_count * 4, kBlock, st, gv, s.tent, s.aggsize, s.left_mid, s.ctr + kCtrLeftMid,
                                                        labels, s.ctr + kCtrErr);
-  k_phase3_block<I><<<c->sm_count * 2, kBlock, 0, st>>>(gv, s.tent, s.aggsize, s.left_heavy,
+  launch_k(c, k_phase3_block<I>, c->sm_count * 2, kBlock, st, gv, s.tent, s.aggsize, s.left_heavy,
                                                         s.ctr + kCtrLeftHeavy, labels, s.ctr + kCtrErr);
   c->launches += 3;
 }

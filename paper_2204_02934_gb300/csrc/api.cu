@@ -21,6 +21,7 @@ void set_error_text(const char* msg) { snprintf(g_last_error, sizeof(g_last_erro
 
 void timer_begin(mis2_ctx* c, int cls, cudaStream_t st) {
   if (!c->cfg.timing) return;
+  if (c->cfg.timing == MIS2_TIMING_LOOP && cls != kKcDeviceLoop) return;  // its timer_end sees no open interval
   Timer& t = c->timer;
   if (t.used + 2 > t.ev.size()) {
     for (int k = 0; k < 64; k++) {
@@ -111,8 +112,9 @@ static int validate_cfg(const mis2_config* cfg) {
   if (cfg->block_size != kBlock) return MIS2_ERR_INVALID_ARG;
   if (cfg->loop != MIS2_LOOP_HOST && cfg->loop != MIS2_LOOP_DEVICE) return MIS2_ERR_INVALID_ARG;
   if (cfg->spin_limit < 1 || cfg->loop_blocks_per_sm < 0) return MIS2_ERR_INVALID_ARG;
+  if (cfg->timing < 0 || cfg->timing > MIS2_TIMING_LOOP) return MIS2_ERR_INVALID_ARG;
   if ((cfg->ablation & ~(MIS2_ABLATE_NO_WORKLISTS | MIS2_ABLATE_TUPLE_ENGINE | MIS2_ABLATE_UNPACKED_TUPLES)) != 0 ||
-      cfg->reserved != 0)
+      (cfg->serial_launches != 0 && cfg->serial_launches != 1))
     return MIS2_ERR_INVALID_ARG;
   return MIS2_OK;
 }

@@ -30,6 +30,7 @@ constexpr int kWarpEntries = 8192;     // larger aggregates go to the block kern
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_hist(GraphView<I> g, const int32_t* labels, int32_t* agg_cnt,
                                                         int32_t* ub) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = lane_id();
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < g.n; base += stride) {
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_hist(GraphView<I> g, const in
 
 __global__ void __launch_bounds__(kBlock) k_coarse_scatter(int64_t n, const int32_t* labels, int32_t* cursor,
                                                            int32_t* members) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int lane = lane_id();
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; base < n; base += stride) {
@@ -239,6 +241,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const i
                                                          const int32_t* agg_ptr, const int32_t* members,
                                                          const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp,
                                                          int32_t* c_cnt) {
+  pdl_enter();
   __shared__ int32_t sh_cnt[kBlock / 32][32];
   __shared__ int32_t sh_sel[kBlock / 32][32];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
@@ -362,6 +365,7 @@ constexpr int kCand = 12;  // candidate slots per vertex: three int4
 
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_cand(GraphView<I> g, const int32_t* labels, int4* cand) {
+  pdl_enter();
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   __shared__ int32_t outs[kBlock / 32][32 * (kCand + 1)];
   const int lane = lane_id();
@@ -425,6 +429,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_merge(int64_t n_aggs, const i
                                                          const int32_t* ub_ptr, const int4* cand, int32_t* tmp,
                                                          int32_t* c_cnt, int32_t* rest, int32_t* rest_cnt,
                                                          bool small_on) {
+  pdl_enter();
   __shared__ int32_t tabs[kBlock / 32][kMergeSlots];
   __shared__ int32_t dcnt[kBlock / 32];
   const int lane = lane_id(), wib = threadIdx.x >> 5;
@@ -548,6 +553,7 @@ __global__ void __launch_bounds__(kCoarseWarps * 32) k_coarse_rows(
     GraphView<I> g, const int32_t* labels, int64_t n_aggs, const int32_t* agg_ptr, const int32_t* members,
     const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp, int32_t* c_cnt, int32_t* large, int32_t* large_cnt,
     bool small_on, const int32_t* list, const int32_t* list_cnt) {
+  pdl_enter();
   __shared__ int32_t sbuf[kCoarseWarps][kSortCap];
   __shared__ __align__(16) int32_t stage[kCoarseWarps][kStageWarpWords];
   __shared__ int32_t scnt[kCoarseWarps];
@@ -648,6 +654,7 @@ __global__ void __launch_bounds__(kBlock) k_large_chunks(const int32_t* large, i
                                                          const int32_t* agg_ptr, int64_t* chunk_off,
                                                          const int32_t* n_large_dev, int32_t* kb_out, int32_t* err,
                                                          int32_t* giant_cnt) {
+  pdl_enter();
   __shared__ int sh[40];
   __shared__ int32_t skb;
   if (threadIdx.x == 0) {
@@ -683,6 +690,7 @@ __global__ void __launch_bounds__(kBlock) k_large_chunks(const int32_t* large, i
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_giant_pieces(GraphView<I> g, const int32_t* giant_v,
                                                          const int32_t* giant_cnt, int64_t* giant_off) {
+  pdl_enter();
   __shared__ int sh[40];
   const int32_t ng = block_load(giant_cnt);
   int64_t acc = 0;
@@ -709,6 +717,7 @@ __global__ void __launch_bounds__(kBlock) k_giant_or(GraphView<I> g, const int32
                                                      int32_t k0, const int32_t* giant_v, const int32_t* giant_slot,
                                                      const int32_t* giant_cnt, const int64_t* giant_off,
                                                      uint32_t* bitmaps, int64_t words) {
+  pdl_enter();
   const int32_t ng = block_load(giant_cnt);
   const int64_t total = block_load(giant_off + ng);
   const int lane = lane_id();
@@ -751,6 +760,7 @@ __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32
                                                      int32_t kb, const int64_t* chunk_off, uint32_t* bitmaps,
                                                      int64_t words, const int32_t* kb_dev, int32_t* giant_v,
                                                      int32_t* giant_slot, int32_t* giant_cnt) {
+  pdl_enter();
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   if (kb_dev != nullptr) kb = block_load(kb_dev);
   const int64_t total = block_load(chunk_off + kb);
@@ -785,6 +795,7 @@ __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32
 __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int32_t k0, int32_t kb,
                                                        const int32_t* ub_ptr, uint32_t* bitmaps, int64_t words,
                                                        int32_t* tmp, int32_t* c_cnt, const int32_t* kb_dev) {
+  pdl_enter();
   constexpr int kW = kBlock / 32;
   __shared__ int64_t wsum[kW];
   if (kb_dev != nullptr) kb = block_load(kb_dev);
@@ -834,6 +845,7 @@ __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int
 
 // Clears the bitmaps of a batch whose size is only known on the device.
 __global__ void __launch_bounds__(kBlock) k_large_zero(uint32_t* bitmaps, int64_t words, const int32_t* kb_dev) {
+  pdl_enter();
   const int64_t total = (int64_t)block_load(kb_dev) * words;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     bitmaps[i] = 0u;
@@ -855,6 +867,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const in
                                                         const int32_t* c_rowptr, const int32_t* tmp,
                                                         int32_t* c_colind, const int32_t* err, const int32_t* total,
                                                         int64_t cap) {
+  pdl_enter();
   if (pack_refused(err, total, cap)) return;
   const int lane = lane_id();
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -873,6 +886,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* larg
                                                              const int32_t* c_rowptr, const int32_t* tmp,
                                                              int32_t* c_colind, const int32_t* err,
                                                              const int32_t* total, int64_t cap) {
+  pdl_enter();
   if (pack_refused(err, total, cap)) return;
   const int64_t nl = block_load(n_large);
   for (int64_t i = blockIdx.x; i < nl; i += gridDim.x) {
@@ -915,7 +929,7 @@ static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t
   Scratch& s = c->s;
   const int rows_blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
   if (small_on) {
-    k_coarse_rows<I><<<rows_blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub,
+    launch_k(c, k_coarse_rows<I>, rows_blocks, kCoarseWarps * 32, st, gv, labels, n_aggs, s.agg_ptr, s.members, s.ub,
                                                                 s.ub_ptr, s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge,
                                                                 small_on, nullptr, nullptr);
     c->launches++;
@@ -923,13 +937,13 @@ static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t
   }
   if (!ctr_fresh) MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
   if (!cand_ready) {
-    k_coarse_cand<I><<<grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
+    launch_k(c, k_coarse_cand<I>, grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, st, gv, labels, s.cand);
     c->launches++;
   }
-  k_coarse_merge<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+  launch_k(c, k_coarse_merge, grid_for(c, n_aggs, kBlock / 32, 8), kBlock, st, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
                                                                           s.cand, s.tmp, s.c_cnt, s.left_mid,
                                                                           s.ctr + kCtrCoarseRest, small_on);
-  k_coarse_rows<I><<<rows_blocks, kCoarseWarps * 32, 0, st>>>(gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+  launch_k(c, k_coarse_rows<I>, rows_blocks, kCoarseWarps * 32, st, gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
                                                               s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on,
                                                               s.left_mid, s.ctr + kCtrCoarseRest);
   c->launches += 2;
@@ -959,15 +973,15 @@ static int coarse_tail(mis2_ctx* c, const GraphView<I>& gv, const int32_t* label
     for (int32_t k0 = k_start; k0 < n_large; k0 += slots) {
       const int32_t kb = std::min(slots, n_large - k0);
       MIS2_CUDA(cudaMemsetAsync(s.bitmaps, 0, (size_t)kb * words * sizeof(uint32_t), st));
-      k_large_chunks<<<1, kBlock, 0, st>>>(s.large, k0, kb, s.agg_ptr, s.chunk_off, nullptr, nullptr, nullptr,
+      launch_k(c, k_large_chunks, 1, kBlock, st, s.large, k0, kb, s.agg_ptr, s.chunk_off, nullptr, nullptr, nullptr,
                                            s.ctr + kCtrGiant);
-      k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, k0, kb,
+      launch_k(c, k_large_or<I>, c->sm_count * 8, kBlock, st, gv, labels, s.agg_ptr, s.members, s.large, k0, kb,
                                                         s.chunk_off, s.bitmaps, words, nullptr, s.giant_v,
                                                         s.giant_slot, s.ctr + kCtrGiant);
-      k_giant_pieces<I><<<1, kBlock, 0, st>>>(gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
-      k_giant_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.large, k0, s.giant_v, s.giant_slot,
+      launch_k(c, k_giant_pieces<I>, 1, kBlock, st, gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
+      launch_k(c, k_giant_or<I>, c->sm_count * 8, kBlock, st, gv, labels, s.large, k0, s.giant_v, s.giant_slot,
                                                         s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
-      k_large_emit<<<std::min<int32_t>(kb, c->sm_count * 2), kBlock, 0, st>>>(s.large, k0, kb, s.ub_ptr, s.bitmaps,
+      launch_k(c, k_large_emit, std::min<int32_t>(kb, c->sm_count * 2), kBlock, st, s.large, k0, kb, s.ub_ptr, s.bitmaps,
                                                                              words, s.tmp, s.c_cnt, nullptr);
       c->launches += 5;
     }
@@ -980,11 +994,11 @@ static int coarse_tail(mis2_ctx* c, const GraphView<I>& gv, const int32_t* label
   const int64_t total = c->h_ctr[kCtrCnnz];
   if (total > c_colind_cap) return MIS2_ERR_INVALID_ARG;
   timer_begin(c, kKcCoarse, st);
-  k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
+  launch_k(c, k_coarse_pack, grid_for(c, n_aggs, kBlock / 32, 8), kBlock, st, n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
                                                                         c_colind, nullptr, nullptr, 0);
   c->launches++;
   if (n_large > 0) {
-    k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
+    launch_k(c, k_coarse_pack_long, c->sm_count * 2, kBlock, st, s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
                                                            s.tmp, c_colind, nullptr, nullptr, 0);
     c->launches++;
   }
@@ -1015,19 +1029,19 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n_aggs * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n_aggs * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLarge, 0, 2 * sizeof(int32_t), st));
-  k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
+  launch_k(c, k_coarse_hist<I>, grid_for(c, n, kBlock), kBlock, st, gv, labels, s.agg_cnt, s.ub);
   c->launches++;
   timer_end(c, st);
   MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st));
   MIS2_TRY(exclusive_scan_i32(c, s.ub, n_aggs, s.ub_ptr, nullptr, st));
   timer_begin(c, kKcCoarse, st);
   MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-  k_coarse_scatter<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, labels, s.cursor, s.members);
+  launch_k(c, k_coarse_scatter, grid_for(c, n, kBlock), kBlock, st, n, labels, s.cursor, s.members);
   // the batched path pays off when small aggregates are common: average
   // entries per aggregate at most half the sub-batch
   const bool small_on = n_aggs < ((int64_t)1 << kSmallLabelBits) && g.nnz <= (int64_t)(kSmallEntries / 2) * n_aggs;
   if (small_on) {
-    k_coarse_small<I><<<grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, 0, st>>>(
+    launch_k(c, k_coarse_small<I>, grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, st, 
         gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
     c->launches++;
   }
@@ -1066,10 +1080,10 @@ static int coarse_prelude_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labe
   timer_begin(c, kKcCoarse, st);
   MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n * sizeof(int32_t), st));
-  k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
+  launch_k(c, k_coarse_hist<I>, grid_for(c, n, kBlock), kBlock, st, gv, labels, s.agg_cnt, s.ub);
   c->launches++;
   if (g.nnz >= (int64_t)kEarlyCandDegree * n) {
-    k_coarse_cand<I><<<grid_for(c, (n + 31) / 32, kBlock / 32, 8), kBlock, 0, st>>>(gv, labels, s.cand);
+    launch_k(c, k_coarse_cand<I>, grid_for(c, (n + 31) / 32, kBlock / 32, 8), kBlock, st, gv, labels, s.cand);
     c->launches++;
     *cand_ready = true;
   }
@@ -1111,7 +1125,7 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
     MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLargeKb, 0, sizeof(int32_t), st));
   }
   if (!prelude_done) {
-    k_coarse_hist<I><<<grid_for(c, n, kBlock), kBlock, 0, st>>>(gv, labels, s.agg_cnt, s.ub);
+    launch_k(c, k_coarse_hist<I>, grid_for(c, n, kBlock), kBlock, st, gv, labels, s.agg_cnt, s.ub);
     c->launches++;
   }
   timer_end(c, st);
@@ -1119,38 +1133,38 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   MIS2_TRY(exclusive_scan_i32(c, s.ub, n_aggs, s.ub_ptr, nullptr, st));
   timer_begin(c, kKcCoarse, st);
   MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-  k_coarse_scatter<<<grid_for(c, n, kBlock), kBlock, 0, st>>>(n, labels, s.cursor, s.members);
+  launch_k(c, k_coarse_scatter, grid_for(c, n, kBlock), kBlock, st, n, labels, s.cursor, s.members);
   // the batched path pays off when small aggregates are common: average
   // entries per aggregate at most half the sub-batch
   const bool small_on = n_aggs < ((int64_t)1 << kSmallLabelBits) && g.nnz <= (int64_t)(kSmallEntries / 2) * n_aggs;
   if (small_on) {
-    k_coarse_small<I><<<grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, 0, st>>>(
+    launch_k(c, k_coarse_small<I>, grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, st, 
         gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
     c->launches++;
   }
   MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st, cand_ready, ctr_fresh));
   const int64_t words = (n_aggs + 31) / 32;
   const int32_t slots = bitmap_slots(c, n_aggs);
-  k_large_chunks<<<1, kBlock, 0, st>>>(s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
+  launch_k(c, k_large_chunks, 1, kBlock, st, s.large, 0, slots, s.agg_ptr, s.chunk_off, s.ctr + kCtrLarge,
                                        s.ctr + kCtrLargeKb, s.ctr + kCtrErr, s.ctr + kCtrGiant);
-  k_large_zero<<<c->sm_count * 2, kBlock, 0, st>>>(s.bitmaps, words, s.ctr + kCtrLargeKb);
-  k_large_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.agg_ptr, s.members, s.large, 0, slots,
+  launch_k(c, k_large_zero, c->sm_count * 2, kBlock, st, s.bitmaps, words, s.ctr + kCtrLargeKb);
+  launch_k(c, k_large_or<I>, c->sm_count * 8, kBlock, st, gv, labels, s.agg_ptr, s.members, s.large, 0, slots,
                                                     s.chunk_off, s.bitmaps, words, s.ctr + kCtrLargeKb, s.giant_v,
                                                     s.giant_slot, s.ctr + kCtrGiant);
-  k_giant_pieces<I><<<1, kBlock, 0, st>>>(gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
-  k_giant_or<I><<<c->sm_count * 8, kBlock, 0, st>>>(gv, labels, s.large, 0, s.giant_v, s.giant_slot,
+  launch_k(c, k_giant_pieces<I>, 1, kBlock, st, gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
+  launch_k(c, k_giant_or<I>, c->sm_count * 8, kBlock, st, gv, labels, s.large, 0, s.giant_v, s.giant_slot,
                                                     s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
-  k_large_emit<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, 0, slots, s.ub_ptr, s.bitmaps, words, s.tmp, s.c_cnt,
+  launch_k(c, k_large_emit, c->sm_count * 2, kBlock, st, s.large, 0, slots, s.ub_ptr, s.bitmaps, words, s.tmp, s.c_cnt,
                                                    s.ctr + kCtrLargeKb);
   c->launches += 7;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
   timer_begin(c, kKcCoarse, st);
-  k_coarse_pack<<<grid_for(c, n_aggs, kBlock / 32, 8), kBlock, 0, st>>>(n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
+  launch_k(c, k_coarse_pack, grid_for(c, n_aggs, kBlock / 32, 8), kBlock, st, n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
                                                                         c_colind, s.ctr + kCtrErr,
                                                                         s.ctr + kCtrCnnz, c_colind_cap);
-  k_coarse_pack_long<<<c->sm_count * 2, kBlock, 0, st>>>(s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
+  launch_k(c, k_coarse_pack_long, c->sm_count * 2, kBlock, st, s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
                                                          s.tmp, c_colind, s.ctr + kCtrErr, s.ctr + kCtrCnnz,
                                                          c_colind_cap);
   c->launches += 2;

@@ -155,6 +155,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // ----------------------------------------------------------------- reductions
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may be scheduled while the preceding kernel of its stream is
+// still running.  pdl_enter() waits until that kernel has completed and its
+// writes are visible (it returns at once for a kernel launched without the
+// attribute), then lets the next kernel's blocks be scheduled.  Every kernel
+// that launch_k starts calls it before touching global memory.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int G>
 __device__ __forceinline__ unsigned group_mask() {
   if constexpr (G == 32) return kFull;

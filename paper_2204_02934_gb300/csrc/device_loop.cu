@@ -225,7 +225,7 @@ static int rounds_device_t(mis2_ctx* c, const GraphArgs& g, const int32_t* label
   la.M = s.M;
   la.ctr = s.ctr;
   la.dtr = s.dtrace + (int64_t)trace_phase * MIS2_TRACE_CAP * 4;
-  la.ts = c->cfg.timing ? s.loop_ts + (int64_t)trace_phase * kLoopTsWords : nullptr;
+  la.ts = c->cfg.timing == MIS2_TIMING_ALL ? s.loop_ts + (int64_t)trace_phase * kLoopTsWords : nullptr;
   la.labels = labels;
   la.spin_limit = c->cfg.spin_limit;
   la.warp_degree = pick_warp_degree(c, g);

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -197,6 +198,26 @@ int timer_collect(mis2_ctx* c);
 int pick_group_lanes(const mis2_ctx* c, const GraphArgs& g);
 int pick_warp_degree(const mis2_ctx* c, const GraphArgs& g);
 int grid_for(const mis2_ctx* c, int64_t items, int items_per_block, int blocks_per_sm = 8);
+// Launch of the short kernels around the MIS-2 loops: with programmatic
+// stream serialisation (unless the configuration asks for serial launches or
+// per-kernel timing) a kernel may be scheduled while the one before it in
+// the stream finishes, which hides most of the gap between dependent
+// launches; each kernel started here begins with pdl_enter().  Errors
+// surface through cudaGetLastError, as with <<< >>>.
+template <typename... P, typename... A>
+inline void launch_k(const mis2_ctx* c, void (*k)(P...), int grid, int block, cudaStream_t st, A&&... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)grid);
+  lc.blockDim = dim3((unsigned)block);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = st;
+  lc.attrs = at;
+  lc.numAttrs = (c->cfg.serial_launches == 0 && c->cfg.timing != MIS2_TIMING_ALL) ? 1 : 0;
+  (void)cudaLaunchKernelEx(&lc, k, std::forward<A>(args)...);
+}
 // Resident blocks per SM of a kernel at `block` threads and `smem` bytes of
 // dynamic shared memory on the context's device
 // (cudaOccupancyMaxActiveBlocksPerMultiprocessor), asked once per (kernel,

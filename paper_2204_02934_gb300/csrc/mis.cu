@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kBlock) k_decide_block(GraphView<I> g, uint32_
 }
 
 __global__ void __launch_bounds__(1024) k_scan_tile_counts(int32_t* tile_cnt, int64_t ntiles, int32_t* total) {
+  pdl_enter();
   __shared__ int sh[40];
   __shared__ int carry_sh;
   if (threadIdx.x == 0) carry_sh = 0;
@@ -387,9 +388,9 @@ int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32
   const int blocks = grid_for(c, nt, 1, 8);
   timer_begin(c, kKcCompact, st);
   const bool direct = nt <= kScanDirectTiles;
-  k_tile_count<PredIn><<<blocks, kBlock, 0, st>>>(n, PredIn{c->s.T}, c->s.tile);
-  if (!direct) k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, count_dev);
-  k_tile_compact<PredIn, EmitRoots><<<blocks, kBlock, 0, st>>>(n, PredIn{c->s.T}, c->s.tile,
+  launch_k(c, k_tile_count<PredIn>, blocks, kBlock, st, n, PredIn{c->s.T}, c->s.tile);
+  if (!direct) launch_k(c, k_scan_tile_counts, 1, 1024, st, c->s.tile, nt, count_dev);
+  launch_k(c, k_tile_compact<PredIn, EmitRoots>, blocks, kBlock, st, n, PredIn{c->s.T}, c->s.tile,
                                                                EmitRoots{roots, flags}, direct, count_dev);
   c->launches += direct ? 2 : 3;
   timer_end(c, st);
@@ -407,9 +408,9 @@ int compact_flags(mis2_ctx* c, const uint8_t* flags, const int32_t* map, int64_t
   const int blocks = grid_for(c, nt, 1, 8);
   timer_begin(c, kKcCompact, st);
   const bool direct = nt <= kScanDirectTiles;
-  k_tile_count<PredFlag><<<blocks, kBlock, 0, st>>>(n, PredFlag{flags}, c->s.tile);
-  if (!direct) k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, count_dev);
-  k_tile_compact<PredFlag, EmitMapped><<<blocks, kBlock, 0, st>>>(n, PredFlag{flags}, c->s.tile,
+  launch_k(c, k_tile_count<PredFlag>, blocks, kBlock, st, n, PredFlag{flags}, c->s.tile);
+  if (!direct) launch_k(c, k_scan_tile_counts, 1, 1024, st, c->s.tile, nt, count_dev);
+  launch_k(c, k_tile_compact<PredFlag, EmitMapped>, blocks, kBlock, st, n, PredFlag{flags}, c->s.tile,
                                                                   EmitMapped{map, out}, direct, count_dev);
   c->launches += direct ? 2 : 3;
   timer_end(c, st);
@@ -428,9 +429,9 @@ int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out
   const int blocks = grid_for(c, nt, 1, 8);
   timer_begin(c, kKcCompact, st);
   const bool direct = nt <= kScanDirectTiles;
-  k_tile_sum<ValArr><<<blocks, kBlock, 0, st>>>(n, ValArr{vals}, c->s.tile);
-  if (!direct) k_scan_tile_counts<<<1, 1024, 0, st>>>(c->s.tile, nt, total_dev);
-  k_tile_scan_write<ValArr, int32_t><<<blocks, kBlock, 0, st>>>(n, ValArr{vals}, c->s.tile, out, direct, total_dev);
+  launch_k(c, k_tile_sum<ValArr>, blocks, kBlock, st, n, ValArr{vals}, c->s.tile);
+  if (!direct) launch_k(c, k_scan_tile_counts, 1, 1024, st, c->s.tile, nt, total_dev);
+  launch_k(c, k_tile_scan_write<ValArr, int32_t>, blocks, kBlock, st, n, ValArr{vals}, c->s.tile, out, direct, total_dev);
   c->launches += direct ? 2 : 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());

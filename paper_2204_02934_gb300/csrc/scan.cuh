@@ -31,6 +31,7 @@ __device__ __forceinline__ int tile_offset(const int32_t* tile_cnt, int64_t tile
 // Pred: struct with `__device__ bool operator()(int64_t i) const`.
 template <class Pred>
 __global__ void __launch_bounds__(kBlock) k_tile_count(int64_t n, Pred pred, int32_t* tile_cnt) {
+  pdl_enter();
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
     int c = 0;
@@ -48,6 +49,7 @@ __global__ void __launch_bounds__(kBlock) k_tile_count(int64_t n, Pred pred, int
 // Val: struct with `__device__ int operator()(int64_t i) const`.
 template <class Val>
 __global__ void __launch_bounds__(kBlock) k_tile_sum(int64_t n, Val val, int32_t* tile_cnt) {
+  pdl_enter();
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
     int c = 0;
@@ -73,6 +75,7 @@ __global__ void __launch_bounds__(1024) k_scan_tile_counts(int32_t* tile_cnt, in
 template <class Pred, class Emit>
 __global__ void __launch_bounds__(kBlock) k_tile_compact(int64_t n, Pred pred, const int32_t* tile_off,
                                                           Emit emit, bool direct, int32_t* total_out) {
+  pdl_enter();
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanIpt;
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(kBlock) k_tile_compact(int64_t n, Pred pred, c
 template <class Val, typename O>
 __global__ void __launch_bounds__(kBlock) k_tile_scan_write(int64_t n, Val val, const int32_t* tile_off,
                                                              O* out, bool direct, int32_t* total_out) {
+  pdl_enter();
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanIpt;

@@ -25,6 +25,7 @@ STATUS = {
 MIS2_AGG_ALG3, MIS2_AGG_BASIC = 0, 1
 MIS2_HASH_XORSHIFT_STAR, MIS2_HASH_XORSHIFT, MIS2_HASH_FIXED = 0, 1, 2
 MIS2_LOOP_HOST, MIS2_LOOP_DEVICE = 0, 1
+MIS2_TIMING_OFF, MIS2_TIMING_ALL, MIS2_TIMING_LOOP = 0, 1, 2
 MIS2_DEBUG_VALIDATE, MIS2_DEBUG_FORCE_TIMEOUT = 0x1, 0x100
 MIS2_ABLATE_NO_WORKLISTS, MIS2_ABLATE_TUPLE_ENGINE, MIS2_ABLATE_UNPACKED_TUPLES = 0x1, 0x2, 0x4
 MIS2_TRACE_CAP = 64
@@ -67,8 +68,8 @@ class mis2_config(ctypes.Structure):
     _fields_ = [("hash_variant", ctypes.c_int32), ("agg_mode", ctypes.c_int32), ("group_lanes", ctypes.c_int32),
                 ("warp_degree", ctypes.c_int32), ("block_degree", ctypes.c_int32), ("block_size", ctypes.c_int32),
                 ("loop", ctypes.c_int32), ("debug_checks", ctypes.c_int32), ("timing", ctypes.c_int32),
-                ("loop_blocks_per_sm", ctypes.c_int32), ("ablation", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("spin_limit", ctypes.c_int64)]
+                ("loop_blocks_per_sm", ctypes.c_int32), ("ablation", ctypes.c_int32),
+                ("serial_launches", ctypes.c_int32), ("spin_limit", ctypes.c_int64)]
 
 
 class mis2_server_config(ctypes.Structure):

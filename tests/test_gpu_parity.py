@@ -355,3 +355,47 @@ def test_workload_rmat_scale22():
     assert g.rowptr.dtype == np.int64
     ctx = make_ctx(g, loop=mis2.MIS2_LOOP_DEVICE)
     assert_level_equal(g, gpu_level(ctx, g, 0), seed=0)
+
+
+def test_overlapped_and_serial_launches_agree():
+    """Programmatic dependent launch (default), serial launches and both
+    timing modes give the same level, equal to the oracle's, and the same
+    full statistics traces, on back-to-back calls of one context."""
+    graphs = [gg.grid3d_27pt(30, 30, 30), gg.rmat(13, 8, seed=3)]
+    ref = {}
+    for serial in (0, 1):
+        for timing in (mis2.MIS2_TIMING_OFF, mis2.MIS2_TIMING_ALL, mis2.MIS2_TIMING_LOOP):
+            ctx = mis2.Context(max(g.n for g in graphs), max(g.nnz for g in graphs), loop=mis2.MIS2_LOOP_DEVICE,
+                               serial_launches=serial, timing=timing)
+            for gi, g in enumerate(graphs):
+                for rep in range(2):
+                    out = gpu_level(ctx, g, 5)
+                    st = ctx.stats()
+                    full = (np.array(st.trace, dtype=np.int64), np.array(st.trace2, dtype=np.int64))
+                    if gi not in ref:
+                        assert_level_equal(g, out, seed=5)
+                        ref[gi] = (out, full)
+                    o0, f0 = ref[gi]
+                    for k in ("in_set", "roots", "labels", "c_rowptr", "c_colind"):
+                        assert np.array_equal(out[k], o0[k]), (serial, timing, gi, k)
+                    assert np.array_equal(full[0], f0[0]) and np.array_equal(full[1], f0[1])
+                    assert not full[0][out["rounds"]:].any() and not full[1][out["rounds2"]:].any()
+            ctx.close()
+
+
+def test_timing_loop_mode_brackets_the_loop_alone():
+    g = gg.grid3d_27pt(24, 24, 24)
+    ctx = mis2.Context(g.n, g.nnz, loop=mis2.MIS2_LOOP_DEVICE, timing=mis2.MIS2_TIMING_LOOP)
+    gpu_level(ctx, g, 0)
+    st = ctx.stats()
+    names = mis2.KERNEL_CLASSES
+    loop = names.index("device_loop")
+    assert st.kernel_ms[loop] > 0 and st.kernel_launches[loop] == 2
+    assert all(st.kernel_ms[k] == 0 for k in range(len(names)) if k != loop)
+    ctx.configure(timing=mis2.MIS2_TIMING_ALL)
+    gpu_level(ctx, g, 0)
+    st = ctx.stats()
+    assert st.kernel_ms[names.index("aggregate")] > 0 and st.kernel_ms[names.index("coarse")] > 0
+    with pytest.raises(mis2.Mis2Error):
+        ctx.configure(timing=3)
+    ctx.close()
