@@ -143,11 +143,14 @@ __global__ void __launch_bounds__(kBlock) k_qualify(GraphView<I> g, const int32_
 // kPhase3SortCap to `heavy`.  The appends of a block's 256 vertices take one
 // reservation per list (one scan of the three counts packed in one word).
 // labels_out (or null): receives tent_v for every aggregated v.
+// fin (or null): the coarse graph's per-aggregate member counts and summed
+// row lengths, started here from the aggregated vertices (phase 3 adds the
+// leftovers), so that the coarse step needs no histogram pass of its own.
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_aggsize_leftovers(GraphView<I> g, const int32_t* tent, int32_t* aggsize,
-                                                              int32_t* labels_out, int32_t* left, int32_t* left_cnt,
-                                                              int32_t* mid, int32_t* mid_cnt, int32_t* heavy,
-                                                              int32_t* heavy_cnt) {
+                                                              int32_t* labels_out, AggCounts fin, int32_t* left,
+                                                              int32_t* left_cnt, int32_t* mid, int32_t* mid_cnt,
+                                                              int32_t* heavy, int32_t* heavy_cnt) {
   pdl_enter();
   __shared__ int sh_scan[40];
   __shared__ int32_t sh_base[3];
@@ -156,14 +159,30 @@ __global__ void __launch_bounds__(kBlock) k_aggsize_leftovers(GraphView<I> g, co
     const int64_t v = base + threadIdx.x;
     const int32_t a = v < g.n ? tent[v] : -2;
     const unsigned peers = __match_any_sync(kFull, a);
-    if (a >= 0 && lane == __ffs(peers) - 1) atomicAdd(aggsize + a, __popc(peers));
-    if (a >= 0 && labels_out != nullptr) labels_out[v] = a;
-    int cls = -1;
-    if (a == -1) {
+    int deg = 0;
+    if (v < g.n && (a == -1 || fin.cnt != nullptr)) {
       int64_t s, e;
       row_range(g, v, s, e);
-      cls = e - s <= kLaneRowMax ? 0 : (e - s <= kPhase3SortCap ? 1 : 2);
+      deg = (int)(e - s);
     }
+    const bool leader = a >= 0 && lane == __ffs(peers) - 1;
+    if (leader) atomicAdd(aggsize + a, __popc(peers));
+    if (fin.cnt != nullptr) {
+      // summed row lengths of the lanes holding the same label
+      int sum = 0;
+#pragma unroll
+      for (int src = 0; src < 32; src++) {
+        const int x = __shfl_sync(kFull, deg, src);
+        if ((peers >> src) & 1u) sum += x;
+      }
+      if (leader) {
+        atomicAdd(fin.cnt + a, __popc(peers));
+        if (sum > 0) atomicAdd(fin.deg + a, sum);
+      }
+    }
+    if (a >= 0 && labels_out != nullptr) labels_out[v] = a;
+    int cls = -1;
+    if (a == -1) cls = deg <= kLaneRowMax ? 0 : (deg <= kPhase3SortCap ? 1 : 2);
     // 10 bits per list: at most 256 entries of each per block
     const int x = cls < 0 ? 0 : 1 << (10 * cls);
     int total;
@@ -243,10 +262,17 @@ __device__ __forceinline__ int32_t phase3_pick(int32_t (&lab)[kLaneRowMax], cons
 // Phase 3, one lane per short leftover row: stage the row, gather its
 // neighbours' tentative labels into registers, and pick the best adjacent
 // aggregate by (max coupling, min size, min id).
+// A leftover of row length deg joins aggregate a: count it into fin.
+__device__ __forceinline__ void fin_add(const AggCounts& fin, int32_t a, int64_t deg) {
+  if (fin.cnt == nullptr || a < 0) return;
+  atomicAdd(fin.cnt + a, 1);
+  if (deg > 0) atomicAdd(fin.deg + a, (int32_t)deg);
+}
+
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
                                                         const int32_t* left, const int32_t* left_cnt, int32_t* labels,
-                                                        int32_t* err) {
+                                                        int32_t* err, AggCounts fin) {
   pdl_enter();
   __shared__ __align__(16) int32_t stage[kBlock / 32][kStageWarpWords];
   const int lane = lane_id();
@@ -284,6 +310,23 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
       labels[v] = best;
       if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
     }
+    if (fin.cnt != nullptr) {
+      // one pair of atomics per aggregate and warp: hub aggregates take
+      // many leftovers
+      const int32_t key = active ? best : -1;
+      const unsigned peers = __match_any_sync(kFull, key);
+      const int deg = active ? (int)(e - s) : 0;
+      int sum = 0;
+#pragma unroll
+      for (int src = 0; src < 32; src++) {
+        const int x = __shfl_sync(kFull, deg, src);
+        if ((peers >> src) & 1u) sum += x;
+      }
+      if (key >= 0 && lane == __ffs(peers) - 1) {
+        atomicAdd(fin.cnt + key, __popc(peers));
+        if (sum > 0) atomicAdd(fin.deg + key, sum);
+      }
+    }
     __syncwarp();
   }
 }
@@ -293,7 +336,7 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_sort(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
                                                         const int32_t* list, const int32_t* list_cnt, int32_t* labels,
-                                                        int32_t* err) {
+                                                        int32_t* err, AggCounts fin) {
   pdl_enter();
   __shared__ int32_t buf[kPhase3SortCap];
   __shared__ uint32_t sh[40];
@@ -357,6 +400,7 @@ __global__ void __launch_bounds__(kBlock) k_phase3_sort(GraphView<I> g, const in
     if (threadIdx.x == 0) {
       const int32_t best = mc > 0 ? (int32_t)ma : -1;
       labels[v] = best;
+      fin_add(fin, best, e - s);
       if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
     }
     __syncthreads();
@@ -368,7 +412,8 @@ __global__ void __launch_bounds__(kBlock) k_phase3_sort(GraphView<I> g, const in
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_phase3_block(GraphView<I> g, const int32_t* tent,
                                                          const int32_t* aggsize, const int32_t* list,
-                                                         const int32_t* list_cnt, int32_t* labels, int32_t* err) {
+                                                         const int32_t* list_cnt, int32_t* labels, int32_t* err,
+                                                         AggCounts fin) {
   pdl_enter();
   __shared__ int cnt[kPhase3Window];
   __shared__ uint32_t sh[40];
@@ -427,6 +472,7 @@ __global__ void __launch_bounds__(kBlock) k_phase3_block(GraphView<I> g, const i
     }
     if (threadIdx.x == 0) {
       labels[v] = best;
+      fin_add(fin, best, e - s);
       if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
     }
     __syncthreads();
@@ -500,26 +546,26 @@ static void launch_qualify(mis2_ctx* c, const GraphView<I>& gv, const int32_t* l
 }
 
 // labels_out: where the aggregated vertices' labels are copied (null: they
-// are there already)
+// are there already); fin: the coarse histogram to start (null: none)
 template <typename I>
-static void launch_leftovers(mis2_ctx* c, const GraphView<I>& gv, cudaStream_t st, int32_t* labels_out = nullptr) {
+static void launch_leftovers(mis2_ctx* c, const GraphView<I>& gv, cudaStream_t st, int32_t* labels_out = nullptr,
+                             AggCounts fin = AggCounts{}) {
   Scratch& s = c->s;
-  launch_k(c, k_aggsize_leftovers<I>, grid_for(c, gv.n, kBlock), kBlock, st, gv, s.tent, s.aggsize, labels_out, s.left,
-                                                                        s.ctr + kCtrLeft, s.left_mid,
-                                                                        s.ctr + kCtrLeftMid, s.left_heavy,
-                                                                        s.ctr + kCtrLeftHeavy);
+  launch_k(c, k_aggsize_leftovers<I>, grid_for(c, gv.n, kBlock), kBlock, st, gv, s.tent, s.aggsize, labels_out, fin,
+           s.left, s.ctr + kCtrLeft, s.left_mid, s.ctr + kCtrLeftMid, s.left_heavy, s.ctr + kCtrLeftHeavy);
   c->launches++;
 }
 
 template <typename I>
-static void launch_phase3(mis2_ctx* c, const GraphView<I>& gv, int32_t* labels, cudaStream_t st) {
+static void launch_phase3(mis2_ctx* c, const GraphView<I>& gv, int32_t* labels, cudaStream_t st,
+                          AggCounts fin = AggCounts{}) {
   Scratch& s = c->s;
-  launch_k(c, k_phase3_lane<I>, grid_for(c, gv.n, kBlock, 8), kBlock, st, gv, s.tent, s.aggsize, s.left, s.ctr + kCtrLeft,
-                                                                     labels, s.ctr + kCtrErr);
+  launch_k(c, k_phase3_lane<I>, grid_for(c, gv.n, kBlock, 8), kBlock, st, gv, s.tent, s.aggsize, s.left,
+           s.ctr + kCtrLeft, labels, s.ctr + kCtrErr, fin);
   launch_k(c, k_phase3_sort<I>, c->sm_count * 4, kBlock, st, gv, s.tent, s.aggsize, s.left_mid, s.ctr + kCtrLeftMid,
-                                                       labels, s.ctr + kCtrErr);
+           labels, s.ctr + kCtrErr, fin);
   launch_k(c, k_phase3_block<I>, c->sm_count * 2, kBlock, st, gv, s.tent, s.aggsize, s.left_heavy,
-                                                        s.ctr + kCtrLeftHeavy, labels, s.ctr + kCtrErr);
+           s.ctr + kCtrLeftHeavy, labels, s.ctr + kCtrErr, fin);
   c->launches += 3;
 }
 
@@ -603,10 +649,13 @@ int agg_phase3(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t total, 
 }
 
 // The level's aggregation without host synchronisation.  The counter words
-// it uses were cleared at the level's start.  Phases 1 and 2 label into
-// s.tent, the frozen labels phase 3 reads; the fused sizes / leftovers pass
-// copies every aggregated vertex's label to `labels`, and phase 3 adds the
-// leftovers' (no device-to-device copy of the labels).
+// it uses were cleared at the level's start, and the level's root
+// compaction has set s.tent to -1 and s.aggsize, s.agg_cnt and s.ub to 0.
+// Phases 1 and 2 label into s.tent, the frozen labels phase 3 reads; the
+// fused sizes / leftovers pass copies every aggregated vertex's label to
+// `labels`, and phase 3 adds the leftovers' (no device-to-device copy of the
+// labels).  The coarse graph's histogram (s.agg_cnt, s.ub) is accumulated on
+// the way.
 template <typename I>
 static int agg_async_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, const PrioCfg& p, int mode,
                        int32_t* labels, cudaStream_t st) {
@@ -614,7 +663,6 @@ static int agg_async_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, co
   const GraphView<I> gv = gview<I>(g);
   const int64_t n = g.n;
   int32_t* tent = s.tent;
-  MIS2_CUDA(cudaMemsetAsync(tent, 0xFF, n * sizeof(int32_t), st));
   timer_begin(c, kKcAggregate, st);
   launch_claim<I>(c, gv, roots, 0, s.ctr + kCtrRoots, tent, 0, st, nullptr, s.ctr + kCtrHeavy);
   timer_end(c, st);
@@ -632,9 +680,9 @@ static int agg_async_t(mis2_ctx* c, const GraphArgs& g, const int32_t* roots, co
     timer_end(c, st);
   }
   timer_begin(c, kKcAggregate, st);
-  MIS2_CUDA(cudaMemsetAsync(s.aggsize, 0, n * sizeof(int32_t), st));
-  launch_leftovers<I>(c, gv, st, labels);
-  launch_phase3<I>(c, gv, labels, st);
+  const AggCounts fin{s.agg_cnt, s.ub};
+  launch_leftovers<I>(c, gv, st, labels, fin);
+  launch_phase3<I>(c, gv, labels, st, fin);
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   return MIS2_OK;

@@ -480,7 +480,14 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
   {
     NvtxRange r("MIS-2 (Algorithm 1)");
     MIS2_TRY(mis2_rounds_device_async(c, ga, nullptr, p, 0, kCtrRounds, st));
-    MIS2_TRY(extract_in_set(c, ga.n, in_set, rl, s.ctr + kCtrRoots, st));
+    // the same pass initialises the aggregation's frozen labels and sizes
+    // and the coarse graph's histogram
+    LevelFill fill;
+    fill.minus1 = s.tent;
+    fill.zero[0] = s.aggsize;
+    fill.zero[1] = s.agg_cnt;
+    fill.zero[2] = s.ub;
+    MIS2_TRY(extract_in_set(c, ga.n, in_set, rl, s.ctr + kCtrRoots, st, fill));
   }
   {
     NvtxRange r("aggregation (Algorithm 3)");
@@ -496,7 +503,7 @@ static int level_fast(mis2_ctx* c, const GraphArgs& ga, uint64_t seed, uint8_t* 
   bool cand_ready = false;
   if (c_rowptr != nullptr) {
     NvtxRange r("coarse graph");
-    MIS2_TRY(coarsen_prelude(c, ga, lab, &cand_ready, st));
+    MIS2_TRY(coarsen_prelude(c, ga, lab, &cand_ready, st, true));
   }
   MIS2_CUDA(cudaEventSynchronize(c->ev_counts));
   MIS2_TRY(device_error(c->h_ctr[kCtrErr]));

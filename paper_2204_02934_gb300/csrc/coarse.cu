@@ -362,6 +362,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const i
 // the merge removes it).  A vertex needing more slots, or with a row longer
 // than 32 entries, gets slot 0 = -2.
 constexpr int kCand = 12;  // candidate slots per vertex: three int4
+constexpr int kMergeRowCap = 1024;  // overflowing member rows the merge walks itself
 
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_cand(GraphView<I> g, const int32_t* labels, int4* cand) {
@@ -417,18 +418,40 @@ __global__ void __launch_bounds__(kBlock) k_coarse_cand(GraphView<I> g, const in
 // to 64 members).  The members' labels from k_coarse_cand go into a
 // shared-memory hash set, one insertion per distinct label per step (lanes
 // holding equal labels are matched first); the set, at most 32 labels, is
-// then sorted across the lanes and written in ascending order.  Aggregates
-// with more members, a member flagged by k_coarse_cand or more than 32
-// distinct labels go to `rest` (the general hash-set kernel); small
+// then sorted across the lanes and written in ascending order.  A member
+// flagged by k_coarse_cand (more labels than its slots, or a row longer than
+// 32) has its row walked by the warp instead, a lane per entry.  Aggregates
+// with more members, a flagged member row longer than kMergeRowCap or more
+// than 32 distinct labels go to `rest` (the general hash-set kernel); small
 // aggregates are k_coarse_small's.
 constexpr int kMergeSlots = 128;
 constexpr int kMergeMembers = 64;
 
-__global__ void __launch_bounds__(kBlock) k_coarse_merge(int64_t n_aggs, const int32_t* agg_ptr,
-                                                         const int32_t* members, const int32_t* ub,
-                                                         const int32_t* ub_ptr, const int4* cand, int32_t* tmp,
-                                                         int32_t* c_cnt, int32_t* rest, int32_t* rest_cnt,
-                                                         bool small_on) {
+// One insertion per distinct label l >= 0 among the lanes into the warp's
+// set tab (kMergeSlots slots, linear probing), counting new labels in *cnt.
+// Every lane of the warp calls it.
+__device__ __forceinline__ void merge_insert(int32_t l, int32_t* tab, int32_t* cnt, int lane) {
+  const unsigned peers = __match_any_sync(kFull, l);
+  if (l >= 0 && lane == __ffs(peers) - 1) {
+    uint32_t h = ((uint32_t)l * 2654435761u) >> 25;
+    for (int probe = 0; probe < kMergeSlots; probe++) {
+      const int32_t old = atomicCAS(tab + h, -1, l);
+      if (old == -1) {
+        atomicAdd(cnt, 1);
+        break;
+      }
+      if (old == l) break;
+      h = (h + 1) & (kMergeSlots - 1);
+    }
+  }
+}
+
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_coarse_merge(GraphView<I> g, const int32_t* labels, int64_t n_aggs,
+                                                         const int32_t* agg_ptr, const int32_t* members,
+                                                         const int32_t* ub, const int32_t* ub_ptr, const int4* cand,
+                                                         int32_t* tmp, int32_t* c_cnt, int32_t* rest,
+                                                         int32_t* rest_cnt, bool small_on) {
   pdl_enter();
   __shared__ int32_t tabs[kBlock / 32][kMergeSlots];
   __shared__ int32_t dcnt[kBlock / 32];
@@ -467,7 +490,6 @@ __global__ void __launch_bounds__(kBlock) k_coarse_merge(int64_t n_aggs, const i
           cs[4 * q + 3] = c.w;
         }
       }
-      bad |= cs[0] == -2;
       // as many steps as the longest list of the warp (lists fill from slot 0)
       int mine = 0;
 #pragma unroll
@@ -476,19 +498,28 @@ __global__ void __launch_bounds__(kBlock) k_coarse_merge(int64_t n_aggs, const i
 #pragma unroll
       for (int t = 0; t < kCand; t++) {
         if (t >= steps) break;  // warp-uniform
-        const int32_t l = cs[t] >= 0 ? cs[t] : -1;
-        const unsigned peers = __match_any_sync(kFull, l);
-        if (l >= 0 && lane == __ffs(peers) - 1) {
-          uint32_t h = ((uint32_t)l * 2654435761u) >> 25;
-          for (int probe = 0; probe < kMergeSlots; probe++) {
-            const int32_t old = atomicCAS(tab + h, -1, l);
-            if (old == -1) {
-              atomicAdd(dcnt + wib, 1);
-              break;
-            }
-            if (old == l) break;
-            h = (h + 1) & (kMergeSlots - 1);
+        merge_insert(cs[t] >= 0 ? cs[t] : -1, tab, dcnt + wib, lane);
+      }
+      // members whose list overflowed (or whose row is longer than 32):
+      // their rows are walked here, one member at a time, a lane per entry
+      unsigned over = __ballot_sync(kFull, cs[0] == -2);
+      while (over != 0u) {  // warp-uniform
+        const int src = __ffs(over) - 1;
+        over &= over - 1u;
+        const int64_t u = members[p0 + m0 + src];
+        int64_t rs, re;
+        row_range(g, u, rs, re);
+        if (re - rs > kMergeRowCap) {
+          bad = true;
+          continue;
+        }
+        for (int64_t pb = rs; pb < re; pb += 32) {  // warp-uniform
+          int32_t l = -1;
+          if (pb + lane < re) {
+            l = labels[g.colind[pb + lane]];
+            if (l == (int32_t)a) l = -1;
           }
+          merge_insert(l, tab, dcnt + wib, lane);
         }
       }
     }
@@ -940,7 +971,8 @@ static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t
     launch_k(c, k_coarse_cand<I>, grid_for(c, (gv.n + 31) / 32, kBlock / 32, 8), kBlock, st, gv, labels, s.cand);
     c->launches++;
   }
-  launch_k(c, k_coarse_merge, grid_for(c, n_aggs, kBlock / 32, 8), kBlock, st, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
+  launch_k(c, k_coarse_merge<I>, grid_for(c, n_aggs, kBlock / 32, 8), kBlock, st, gv, labels, n_aggs, s.agg_ptr,
+           s.members, s.ub, s.ub_ptr,
                                                                           s.cand, s.tmp, s.c_cnt, s.left_mid,
                                                                           s.ctr + kCtrCoarseRest, small_on);
   launch_k(c, k_coarse_rows<I>, rows_blocks, kCoarseWarps * 32, st, gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr,
@@ -1032,10 +1064,9 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   launch_k(c, k_coarse_hist<I>, grid_for(c, n, kBlock), kBlock, st, gv, labels, s.agg_cnt, s.ub);
   c->launches++;
   timer_end(c, st);
-  MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st));
+  MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st, s.cursor));
   MIS2_TRY(exclusive_scan_i32(c, s.ub, n_aggs, s.ub_ptr, nullptr, st));
   timer_begin(c, kKcCoarse, st);
-  MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   launch_k(c, k_coarse_scatter, grid_for(c, n, kBlock), kBlock, st, n, labels, s.cursor, s.members);
   // the batched path pays off when small aggregates are common: average
   // entries per aggregate at most half the sub-batch
@@ -1071,17 +1102,19 @@ constexpr int kEarlyCandDegree = 20;
 
 template <typename I>
 static int coarse_prelude_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool hist_done) {
   Scratch& s = c->s;
   const GraphView<I> gv = gview_of<I>(g);
   const int64_t n = g.n;
   *cand_ready = false;
   if (n == 0) return MIS2_OK;
   timer_begin(c, kKcCoarse, st);
-  MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n * sizeof(int32_t), st));
-  MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n * sizeof(int32_t), st));
-  launch_k(c, k_coarse_hist<I>, grid_for(c, n, kBlock), kBlock, st, gv, labels, s.agg_cnt, s.ub);
-  c->launches++;
+  if (!hist_done) {
+    MIS2_CUDA(cudaMemsetAsync(s.agg_cnt, 0, n * sizeof(int32_t), st));
+    MIS2_CUDA(cudaMemsetAsync(s.ub, 0, n * sizeof(int32_t), st));
+    launch_k(c, k_coarse_hist<I>, grid_for(c, n, kBlock), kBlock, st, gv, labels, s.agg_cnt, s.ub);
+    c->launches++;
+  }
   if (g.nnz >= (int64_t)kEarlyCandDegree * n) {
     launch_k(c, k_coarse_cand<I>, grid_for(c, (n + 31) / 32, kBlock / 32, 8), kBlock, st, gv, labels, s.cand);
     c->launches++;
@@ -1092,9 +1125,10 @@ static int coarse_prelude_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labe
   return MIS2_OK;
 }
 
-int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st) {
-  return g.rp64 ? coarse_prelude_t<int64_t>(c, g, labels, cand_ready, st)
-                : coarse_prelude_t<int32_t>(c, g, labels, cand_ready, st);
+int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st,
+                    bool hist_done) {
+  return g.rp64 ? coarse_prelude_t<int64_t>(c, g, labels, cand_ready, st, hist_done)
+                : coarse_prelude_t<int32_t>(c, g, labels, cand_ready, st, hist_done);
 }
 
 template <typename I>
@@ -1129,10 +1163,9 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
     c->launches++;
   }
   timer_end(c, st);
-  MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st));
+  MIS2_TRY(exclusive_scan_i32(c, s.agg_cnt, n_aggs, s.agg_ptr, nullptr, st, s.cursor));
   MIS2_TRY(exclusive_scan_i32(c, s.ub, n_aggs, s.ub_ptr, nullptr, st));
   timer_begin(c, kKcCoarse, st);
-  MIS2_CUDA(cudaMemcpyAsync(s.cursor, s.agg_ptr, n_aggs * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
   launch_k(c, k_coarse_scatter, grid_for(c, n, kBlock), kBlock, st, n, labels, s.cursor, s.members);
   // the batched path pays off when small aggregates are common: average
   // entries per aggregate at most half the sub-batch

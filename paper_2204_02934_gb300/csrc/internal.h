@@ -237,14 +237,28 @@ int mis2_rounds_device(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, c
 // errors accumulate in ctr[kCtrErr] (cleared by the caller).
 int mis2_rounds_device_async(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, const PrioCfg& p,
                              int trace_phase, int rounds_slot, cudaStream_t st);
+// Per-aggregate member counts and summed member row lengths of the coarse
+// graph (its histogram), accumulated by the level path's aggregation
+// kernels when not null.
+struct AggCounts {
+  int32_t* cnt = nullptr;
+  int32_t* deg = nullptr;
+};
+// Arrays of n words the root compaction also initialises (null: none):
+// minus1[v] = -1, zero[k][v] = 0 (the level path's frozen labels and
+// per-aggregate counters, set in the pass that visits every vertex anyway).
+struct LevelFill {
+  int32_t* minus1 = nullptr;
+  int32_t* zero[3] = {nullptr, nullptr, nullptr};
+};
 // Ordered compaction of {v : T_v = IN}: ascending roots, flags, count on
-// device at ctr[kCtrRoots + which] (which: 0 roots, 1 phase-2 roots).
+// device at *count_dev; fills `fill`.
 int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32_t* count_dev,
-                   cudaStream_t st);
+                   cudaStream_t st, const LevelFill& fill = LevelFill{});
 // Exclusive scan of vals[0, n) into out[0, n], out[n] = total; total also
-// stored at *total_dev when not null.
+// stored at *total_dev, and out[0, n) copied to out2, when not null.
 int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out, int32_t* total_dev,
-                       cudaStream_t st);
+                       cudaStream_t st, int32_t* out2 = nullptr);
 // Ordered compaction of indices j < n with flags[j] != 0 mapped through
 // map[j] (map null: j itself) into out; count to *count_dev.
 int compact_flags(mis2_ctx* c, const uint8_t* flags, const int32_t* map, int64_t n, int32_t* out,
@@ -272,7 +286,9 @@ int coarsen_fast(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int64_t
                  bool cand_ready = false, bool ctr_fresh = false);
 // The labels-only first steps of coarsen_fast, queued before n_aggs is known
 // on the host (then pass prelude_done = true and the returned cand_ready).
-int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st);
+// hist_done: the aggregation already left the histogram (s.agg_cnt, s.ub).
+int coarsen_prelude(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, bool* cand_ready, cudaStream_t st,
+                    bool hist_done = false);
 bool coarsen_fast_needs_retry(const mis2_ctx* c);
 // Debug-mode validation (synchronises): MIS2_ERR_BAD_GRAPH for a malformed or
 // asymmetric CSR, or for roots that are not ascending and pairwise more than

@@ -143,9 +143,14 @@ struct PredIn {
 struct EmitRoots {
   int32_t* roots;
   uint8_t* flags;
+  LevelFill fill;
   __device__ void operator()(int64_t i, int32_t pos, bool keep) const {
     if (flags != nullptr) flags[i] = keep ? 1 : 0;
     if (keep && roots != nullptr) roots[pos] = (int32_t)i;
+    if (fill.minus1 != nullptr) fill.minus1[i] = -1;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      if (fill.zero[k] != nullptr) fill.zero[k][i] = 0;
   }
 };
 struct PredFlag {
@@ -379,7 +384,8 @@ int mis2_rounds_host(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, con
                 : rounds_host_t<int32_t>(c, g, labels, p, trace_phase, st, rounds);
 }
 
-int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32_t* count_dev, cudaStream_t st) {
+int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32_t* count_dev, cudaStream_t st,
+                   const LevelFill& fill) {
   if (n == 0) {
     MIS2_CUDA(cudaMemsetAsync(count_dev, 0, sizeof(int32_t), st));
     return MIS2_OK;
@@ -391,7 +397,7 @@ int extract_in_set(mis2_ctx* c, int64_t n, uint8_t* flags, int32_t* roots, int32
   launch_k(c, k_tile_count<PredIn>, blocks, kBlock, st, n, PredIn{c->s.T}, c->s.tile);
   if (!direct) launch_k(c, k_scan_tile_counts, 1, 1024, st, c->s.tile, nt, count_dev);
   launch_k(c, k_tile_compact<PredIn, EmitRoots>, blocks, kBlock, st, n, PredIn{c->s.T}, c->s.tile,
-                                                               EmitRoots{roots, flags}, direct, count_dev);
+                                                               EmitRoots{roots, flags, fill}, direct, count_dev);
   c->launches += direct ? 2 : 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
@@ -419,7 +425,7 @@ int compact_flags(mis2_ctx* c, const uint8_t* flags, const int32_t* map, int64_t
 }
 
 int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out, int32_t* total_dev,
-                       cudaStream_t st) {
+                       cudaStream_t st, int32_t* out2) {
   if (n == 0) {
     MIS2_CUDA(cudaMemsetAsync(out, 0, sizeof(int32_t), st));
     if (total_dev) MIS2_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(int32_t), st));
@@ -431,7 +437,8 @@ int exclusive_scan_i32(mis2_ctx* c, const int32_t* vals, int64_t n, int32_t* out
   const bool direct = nt <= kScanDirectTiles;
   launch_k(c, k_tile_sum<ValArr>, blocks, kBlock, st, n, ValArr{vals}, c->s.tile);
   if (!direct) launch_k(c, k_scan_tile_counts, 1, 1024, st, c->s.tile, nt, total_dev);
-  launch_k(c, k_tile_scan_write<ValArr, int32_t>, blocks, kBlock, st, n, ValArr{vals}, c->s.tile, out, direct, total_dev);
+  launch_k(c, k_tile_scan_write<ValArr, int32_t>, blocks, kBlock, st, n, ValArr{vals}, c->s.tile, out, out2, direct,
+           total_dev);
   c->launches += direct ? 2 : 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());

@@ -103,10 +103,11 @@ __global__ void __launch_bounds__(kBlock) k_tile_compact(int64_t n, Pred pred, c
 }
 
 // Exclusive scan of val(i) into out[i] (i < n), with out[n] = total.
-// direct and *total_out: as for k_tile_compact.
+// direct and *total_out: as for k_tile_compact; out2 (or null) receives a
+// copy of out[0, n).
 template <class Val, typename O>
 __global__ void __launch_bounds__(kBlock) k_tile_scan_write(int64_t n, Val val, const int32_t* tile_off,
-                                                             O* out, bool direct, int32_t* total_out) {
+                                                             O* out, O* out2, bool direct, int32_t* total_out) {
   pdl_enter();
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
@@ -126,7 +127,10 @@ __global__ void __launch_bounds__(kBlock) k_tile_scan_write(int64_t n, Val val, 
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
       const int64_t i = base + k;
-      if (i < n) out[i] = (O)pos;
+      if (i < n) {
+        out[i] = (O)pos;
+        if (out2 != nullptr) out2[i] = (O)pos;
+      }
       pos += v[k];
     }
     if (base <= n - 1 && n - 1 < base + kScanIpt) out[n] = (O)pos;  // thread holding the last item
