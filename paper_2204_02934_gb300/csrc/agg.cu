@@ -331,6 +331,90 @@ __global__ void __launch_bounds__(kBlock) k_phase3_lane(GraphView<I> g, const in
   }
 }
 
+// Phase 3, one warp per medium leftover row of up to kP3WarpMax entries:
+// count its neighbours' tentative labels in a shared-memory hash table of
+// the warp (one insertion per distinct label per step, the count added
+// with it), then reduce the best entry by (max coupling, min size, min id).
+// Longer rows are passed on to `longer` for the block kernel.
+constexpr int kP3WarpMax = 256;
+constexpr int kP3WarpSlots = 512;  // at most half full
+
+template <typename I>
+__global__ void __launch_bounds__(kBlock) k_phase3_warp(GraphView<I> g, const int32_t* tent, const int32_t* aggsize,
+                                                        const int32_t* list, const int32_t* list_cnt, int32_t* labels,
+                                                        int32_t* err, AggCounts fin, int32_t* longer,
+                                                        int32_t* longer_cnt) {
+  pdl_enter();
+  __shared__ int32_t keys[kBlock / 32][kP3WarpSlots];
+  __shared__ int32_t cnts[kBlock / 32][kP3WarpSlots];
+  const int lane = lane_id(), wib = threadIdx.x >> 5;
+  int32_t* K = keys[wib];
+  int32_t* C = cnts[wib];
+  const int64_t n_items = block_load(list_cnt);
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += nw) {
+    const int32_t v = list[it];
+    int64_t s, e;
+    row_range(g, v, s, e);
+    if (e - s > kP3WarpMax) {  // warp-uniform
+      if (lane == 0) longer[atomicAdd(longer_cnt, 1)] = v;
+      continue;
+    }
+#pragma unroll
+    for (int j = lane; j < kP3WarpSlots; j += 32) {
+      K[j] = -1;
+      C[j] = 0;
+    }
+    __syncwarp();
+    for (int64_t pb = s; pb < e; pb += 32) {  // warp-uniform
+      int32_t t = -1;
+      if (pb + lane < e) {
+        const int32_t w = g.colind[pb + lane];
+        t = w != v ? tent[w] : -1;
+      }
+      const unsigned peers = __match_any_sync(kFull, t);
+      if (t >= 0 && lane == __ffs(peers) - 1) {
+        uint32_t h = ((uint32_t)t * 2654435761u) >> 23;  // 9 bits
+        for (int probe = 0; probe < kP3WarpSlots; probe++) {
+          const int32_t old = atomicCAS(K + h, -1, t);
+          if (old == -1 || old == t) {
+            atomicAdd(C + h, __popc(peers));
+            break;
+          }
+          h = (h + 1) & (kP3WarpSlots - 1);
+        }
+      }
+    }
+    __syncwarp();
+    int32_t ka[kP3WarpSlots / 32], sz[kP3WarpSlots / 32];
+#pragma unroll
+    for (int r = 0; r < kP3WarpSlots / 32; r++) {
+      ka[r] = K[lane + 32 * r];
+      sz[r] = ka[r] >= 0 ? __ldg(aggsize + ka[r]) : 0;
+    }
+    int32_t la = -1;
+    int lc = 0, ls = 0;
+#pragma unroll
+    for (int r = 0; r < kP3WarpSlots / 32; r++)
+      if (ka[r] >= 0 && better(C[lane + 32 * r], sz[r], ka[r], lc, ls, la)) {
+        la = ka[r];
+        lc = C[lane + 32 * r];
+        ls = sz[r];
+      }
+    const uint32_t mc = __reduce_max_sync(kFull, la >= 0 ? (uint32_t)lc : 0u);
+    const uint32_t ms = __reduce_min_sync(kFull, la >= 0 && (uint32_t)lc == mc ? (uint32_t)ls : 0xFFFFFFFFu);
+    const uint32_t ma =
+        __reduce_min_sync(kFull, la >= 0 && (uint32_t)lc == mc && (uint32_t)ls == ms ? (uint32_t)la : 0xFFFFFFFFu);
+    if (lane == 0) {
+      const int32_t best = mc > 0 ? (int32_t)ma : -1;
+      labels[v] = best;
+      fin_add(fin, best, e - s);
+      if (best < 0) atomicOr(err, kErrNoAggregatedNeighbour);
+    }
+    __syncwarp();  // the table is cleared for the next row
+  }
+}
+
 // Phase 3, one block per medium leftover row: sort its neighbours'
 // tentative labels in shared memory, count each run, reduce the best run.
 template <typename I>
@@ -562,11 +646,15 @@ static void launch_phase3(mis2_ctx* c, const GraphView<I>& gv, int32_t* labels, 
   Scratch& s = c->s;
   launch_k(c, k_phase3_lane<I>, grid_for(c, gv.n, kBlock, 8), kBlock, st, gv, s.tent, s.aggsize, s.left,
            s.ctr + kCtrLeft, labels, s.ctr + kCtrErr, fin);
-  launch_k(c, k_phase3_sort<I>, c->sm_count * 4, kBlock, st, gv, s.tent, s.aggsize, s.left_mid, s.ctr + kCtrLeftMid,
+  // medium rows: a warp each up to kP3WarpMax entries, the longer ones
+  // (passed on through s.roots2, free by now) a block each
+  launch_k(c, k_phase3_warp<I>, grid_for(c, gv.n, kBlock / 32, 4), kBlock, st, gv, s.tent, s.aggsize, s.left_mid,
+           s.ctr + kCtrLeftMid, labels, s.ctr + kCtrErr, fin, s.roots2, s.ctr + kCtrLeftLong);
+  launch_k(c, k_phase3_sort<I>, c->sm_count * 4, kBlock, st, gv, s.tent, s.aggsize, s.roots2, s.ctr + kCtrLeftLong,
            labels, s.ctr + kCtrErr, fin);
   launch_k(c, k_phase3_block<I>, c->sm_count * 2, kBlock, st, gv, s.tent, s.aggsize, s.left_heavy,
            s.ctr + kCtrLeftHeavy, labels, s.ctr + kCtrErr, fin);
-  c->launches += 3;
+  c->launches += 4;
 }
 
 template <typename I>
@@ -621,6 +709,7 @@ static int phase3_t(mis2_ctx* c, const GraphArgs& g, int32_t* labels, int64_t to
   MIS2_CUDA(cudaMemsetAsync(s.aggsize, 0, std::max<int64_t>(total, 1) * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeft, 0, 2 * sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftMid, 0, sizeof(int32_t), st));
+  MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrLeftLong, 0, sizeof(int32_t), st));
   MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrErr, 0, sizeof(int32_t), st));
   launch_leftovers<I>(c, gv, st);
   launch_phase3<I>(c, gv, labels, st);

@@ -47,6 +47,7 @@ enum : int {
   kCtrRounds2 = 32,  // rounds of the phase-2 device loop
   kCtrLargeKb = 33,  // large aggregates handled in the first bitmap batch
   kCtrGiant = 34,    // giant member rows of the current bitmap batch
+  kCtrLeftLong = 35,  // phase-3 medium leftovers too long for a warp
   kCtrCheckSums = 36,  // debug checks: two 64-bit entry-hash sums (words 36-39)
   kCtrInitSizes = 40,  // no-worklist mode of the host loop: round-0 list sizes (words 40-45)
   kCtrColorLeft = 48,  // colouring: uncoloured count after each round of a batch (words 48-55)
