@@ -819,36 +819,70 @@ __global__ void __launch_bounds__(kBlock) k_large_or(GraphView<I> g, const int32
   }
 }
 
-// One block per bitmap: each warp owns a contiguous run of words; a first
-// pass counts the set bits per warp (one block-level exchange per bitmap),
-// a second writes the labels of the warp's non-zero words in ascending order
-// behind the counts of the warps before it, and clears those words.
+// The bitmaps are emitted in segments of kEmitSeg words, a block per
+// (bitmap, segment) pair, so that the bitmap of a hub aggregate (millions of
+// set bits) is spread over the grid.  k_large_count: the set bits of every
+// pair, seg_cnt[i * nseg + sg].
+constexpr int64_t kEmitSeg = 4096;
+
+__global__ void __launch_bounds__(kBlock) k_large_count(int32_t kb, const uint32_t* bitmaps, int64_t words, int nseg,
+                                                        int32_t* seg_cnt, const int32_t* kb_dev) {
+  pdl_enter();
+  __shared__ int sh[40];
+  if (kb_dev != nullptr) kb = block_load(kb_dev);
+  for (int64_t pr = blockIdx.x; pr < (int64_t)kb * nseg; pr += gridDim.x) {
+    const int64_t i = pr / nseg, sg = pr % nseg;
+    const uint32_t* bm = bitmaps + i * words;
+    const int64_t j0 = sg * kEmitSeg, j1 = min(words, j0 + kEmitSeg);
+    int c = 0;
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) c += __popc(bm[j]);
+    c = block_sum_i32(c, sh);
+    if (threadIdx.x == 0) seg_cnt[pr] = c;
+  }
+}
+
+// A block per (bitmap, segment): each warp owns a contiguous run of the
+// segment's words; the warps' counts are exchanged once, then each warp
+// writes the labels of its non-zero words in ascending order behind the
+// segments and warps before it, and clears those words.  The block of a
+// bitmap's first segment writes the row length.
 __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int32_t k0, int32_t kb,
                                                        const int32_t* ub_ptr, uint32_t* bitmaps, int64_t words,
-                                                       int32_t* tmp, int32_t* c_cnt, const int32_t* kb_dev) {
+                                                       int nseg, const int32_t* seg_cnt, int32_t* tmp,
+                                                       int32_t* c_cnt, const int32_t* kb_dev) {
   pdl_enter();
   constexpr int kW = kBlock / 32;
   __shared__ int64_t wsum[kW];
+  __shared__ int64_t sbase, stotal;
   if (kb_dev != nullptr) kb = block_load(kb_dev);
   const int lane = lane_id(), w = threadIdx.x >> 5;
-  const int64_t seg = ((words + kW - 1) / kW + 31) / 32 * 32;
-  const int64_t w0 = min(words, (int64_t)w * seg), w1 = min(words, w0 + seg);
-  for (int i = blockIdx.x; i < kb; i += gridDim.x) {
+  for (int64_t pr = blockIdx.x; pr < (int64_t)kb * nseg; pr += gridDim.x) {
+    const int64_t i = pr / nseg, sg = pr % nseg;
     const int32_t a = large[k0 + i];
-    uint32_t* bm = bitmaps + (int64_t)i * words;
-    const int64_t out = ub_ptr[a];
+    uint32_t* bm = bitmaps + i * words;
+    const int64_t s0 = sg * kEmitSeg, s1 = min(words, s0 + kEmitSeg);
+    const int64_t seg = ((s1 - s0 + kW - 1) / kW + 31) / 32 * 32;
+    const int64_t w0 = min(s1, s0 + (int64_t)w * seg), w1 = min(s1, w0 + seg);
+    if (threadIdx.x == 0) {
+      int64_t b = 0, t = 0;
+      for (int k = 0; k < nseg; k++) {
+        const int64_t x = seg_cnt[i * nseg + k];
+        b += k < sg ? x : 0;
+        t += x;
+      }
+      sbase = b;
+      stotal = t;
+    }
     int64_t cnt = 0;
     for (int64_t j = w0 + lane; j < w1; j += 32) cnt += __popc(bm[j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
     if (lane == 0) wsum[w] = cnt;
     __syncthreads();
-    int64_t run = 0, total = 0;
+    const int64_t out = ub_ptr[a] + sbase;
+    int64_t run = 0;
 #pragma unroll
-    for (int k = 0; k < kW; k++) {
-      run += k < w ? wsum[k] : 0;
-      total += wsum[k];
-    }
+    for (int k = 0; k < kW; k++) run += k < w ? wsum[k] : 0;
     for (int64_t j0 = w0; j0 < w1; j0 += 32) {
       const int64_t j = j0 + lane;
       uint32_t x = j < w1 ? bm[j] : 0u;
@@ -869,7 +903,7 @@ __global__ void __launch_bounds__(kBlock) k_large_emit(const int32_t* large, int
       }
       run += __shfl_sync(kFull, incl, 31);
     }
-    if (threadIdx.x == 0) c_cnt[a] = (int32_t)total;
+    if (sg == 0 && threadIdx.x == 0) c_cnt[a] = (int32_t)stotal;
     __syncthreads();
   }
 }
@@ -910,22 +944,57 @@ __global__ void __launch_bounds__(kBlock) k_coarse_pack(int64_t n_aggs, const in
   }
 }
 
-// Rows longer than kPackWarpMax (only large aggregates have them): a block
-// per row.
-__global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* large, const int32_t* n_large,
-                                                             const int32_t* ub_ptr, const int32_t* c_cnt,
-                                                             const int32_t* c_rowptr, const int32_t* tmp,
-                                                             int32_t* c_colind, const int32_t* err,
-                                                             const int32_t* total, int64_t cap) {
+// Rows longer than kPackWarpMax (only large aggregates have them) are
+// copied in chunks of kPackChunk entries, a block per chunk, so that one hub
+// row of millions of entries is spread over the grid.  k_pack_chunks (one
+// block) lays the chunks out: chunk_off[i] = chunks of the large rows before
+// i, chunk_off[n_large] = all of them.
+constexpr int64_t kPackChunk = 16384;
+
+__global__ void __launch_bounds__(kBlock) k_pack_chunks(const int32_t* large, const int32_t* n_large,
+                                                        const int32_t* c_cnt, int64_t* chunk_off, const int32_t* err,
+                                                        const int32_t* total, int64_t cap) {
   pdl_enter();
   if (pack_refused(err, total, cap)) return;
-  const int64_t nl = block_load(n_large);
-  for (int64_t i = blockIdx.x; i < nl; i += gridDim.x) {
-    const int32_t a = large[i];
+  __shared__ int sh[40];
+  const int32_t nl = block_load(n_large);
+  int64_t acc = 0;
+  for (int32_t t0 = 0; t0 < nl; t0 += kBlock) {
+    const int32_t i = t0 + (int32_t)threadIdx.x;
+    int ch = 0;
+    if (i < nl) {
+      const int64_t len = c_cnt[large[i]];
+      ch = len > kPackWarpMax ? (int)((len + kPackChunk - 1) / kPackChunk) : 0;
+    }
+    int tile_total;
+    const int x = block_exclusive_scan(ch, sh, &tile_total);
+    if (i < nl) chunk_off[i] = acc + x;
+    acc += tile_total;
+  }
+  if (threadIdx.x == 0) chunk_off[nl] = acc;
+}
+
+__global__ void __launch_bounds__(kBlock) k_coarse_pack_long(const int32_t* large, const int32_t* n_large,
+                                                             const int64_t* chunk_off, const int32_t* ub_ptr,
+                                                             const int32_t* c_cnt, const int32_t* c_rowptr,
+                                                             const int32_t* tmp, int32_t* c_colind,
+                                                             const int32_t* err, const int32_t* total, int64_t cap) {
+  pdl_enter();
+  if (pack_refused(err, total, cap)) return;
+  const int32_t nl = block_load(n_large);
+  const int64_t n_ch = block_load(chunk_off + nl);
+  for (int64_t ch = blockIdx.x; ch < n_ch; ch += gridDim.x) {
+    int lo = 0, hi = nl;  // the last row i with chunk_off[i] <= ch: the one holding chunk ch
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (chunk_off[mid] <= ch) lo = mid;
+      else hi = mid;
+    }
+    const int32_t a = large[lo];
     const int64_t len = c_cnt[a];
-    if (len <= kPackWarpMax) continue;
+    const int64_t k0 = (ch - chunk_off[lo]) * kPackChunk, k1 = min(len, k0 + kPackChunk);
     const int64_t src = ub_ptr[a], dst = c_rowptr[a];
-    for (int64_t k = threadIdx.x; k < len; k += blockDim.x) c_colind[dst + k] = tmp[src + k];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) c_colind[dst + k] = tmp[src + k];
   }
 }
 
@@ -991,6 +1060,15 @@ static int32_t bitmap_slots(const mis2_ctx* c, int64_t n_aggs) {
                                                           std::max<int64_t>(n_aggs, 1)));
 }
 
+// Segments per bitmap of the emit: kEmitSeg words each, unless the
+// (bitmap, segment) counts would not fit the n + 1 words of s.cursor (free
+// by then), in which case one segment per bitmap.
+static int emit_segments(const mis2_ctx* c, int64_t n_aggs) {
+  const int64_t words = (std::max<int64_t>(n_aggs, 1) + 31) / 32;
+  const int64_t nseg = (words + kEmitSeg - 1) / kEmitSeg;
+  return (int64_t)bitmap_slots(c, n_aggs) * nseg <= c->max_n + 1 ? (int)nseg : 1;
+}
+
 // Large aggregates k_start..n_large-1 in batches of bitmaps, then the row
 // offsets (one host read of the total) and the packed colind.
 template <typename I>
@@ -1013,9 +1091,11 @@ static int coarse_tail(mis2_ctx* c, const GraphView<I>& gv, const int32_t* label
       launch_k(c, k_giant_pieces<I>, 1, kBlock, st, gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
       launch_k(c, k_giant_or<I>, c->sm_count * 8, kBlock, st, gv, labels, s.large, k0, s.giant_v, s.giant_slot,
                                                         s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
-      launch_k(c, k_large_emit, std::min<int32_t>(kb, c->sm_count * 2), kBlock, st, s.large, k0, kb, s.ub_ptr, s.bitmaps,
-                                                                             words, s.tmp, s.c_cnt, nullptr);
-      c->launches += 5;
+      const int nseg = emit_segments(c, n_aggs);
+      launch_k(c, k_large_count, c->sm_count * 4, kBlock, st, kb, s.bitmaps, words, nseg, s.cursor, nullptr);
+      launch_k(c, k_large_emit, c->sm_count * 4, kBlock, st, s.large, k0, kb, s.ub_ptr, s.bitmaps, words, nseg,
+               s.cursor, s.tmp, s.c_cnt, nullptr);
+      c->launches += 6;
     }
     timer_end(c, st);
     MIS2_CUDA(cudaGetLastError());
@@ -1030,9 +1110,10 @@ static int coarse_tail(mis2_ctx* c, const GraphView<I>& gv, const int32_t* label
                                                                         c_colind, nullptr, nullptr, 0);
   c->launches++;
   if (n_large > 0) {
-    launch_k(c, k_coarse_pack_long, c->sm_count * 2, kBlock, st, s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
-                                                           s.tmp, c_colind, nullptr, nullptr, 0);
-    c->launches++;
+    launch_k(c, k_pack_chunks, 1, kBlock, st, s.large, s.ctr + kCtrLarge, s.c_cnt, s.chunk_off, nullptr, nullptr, 0);
+    launch_k(c, k_coarse_pack_long, c->sm_count * 4, kBlock, st, s.large, s.ctr + kCtrLarge, s.chunk_off, s.ub_ptr,
+             s.c_cnt, c_rowptr, s.tmp, c_colind, nullptr, nullptr, 0);
+    c->launches += 2;
   }
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
@@ -1187,9 +1268,12 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   launch_k(c, k_giant_pieces<I>, 1, kBlock, st, gv, s.giant_v, s.ctr + kCtrGiant, s.giant_off);
   launch_k(c, k_giant_or<I>, c->sm_count * 8, kBlock, st, gv, labels, s.large, 0, s.giant_v, s.giant_slot,
                                                     s.ctr + kCtrGiant, s.giant_off, s.bitmaps, words);
-  launch_k(c, k_large_emit, c->sm_count * 2, kBlock, st, s.large, 0, slots, s.ub_ptr, s.bitmaps, words, s.tmp, s.c_cnt,
-                                                   s.ctr + kCtrLargeKb);
-  c->launches += 7;
+  const int nseg = emit_segments(c, n_aggs);
+  launch_k(c, k_large_count, c->sm_count * 4, kBlock, st, slots, s.bitmaps, words, nseg, s.cursor,
+           s.ctr + kCtrLargeKb);
+  launch_k(c, k_large_emit, c->sm_count * 4, kBlock, st, s.large, 0, slots, s.ub_ptr, s.bitmaps, words, nseg, s.cursor,
+           s.tmp, s.c_cnt, s.ctr + kCtrLargeKb);
+  c->launches += 8;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   MIS2_TRY(exclusive_scan_i32(c, s.c_cnt, n_aggs, c_rowptr, s.ctr + kCtrCnnz, st));
@@ -1197,10 +1281,11 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   launch_k(c, k_coarse_pack, grid_for(c, n_aggs, kBlock / 32, 8), kBlock, st, n_aggs, s.ub_ptr, s.c_cnt, c_rowptr, s.tmp,
                                                                         c_colind, s.ctr + kCtrErr,
                                                                         s.ctr + kCtrCnnz, c_colind_cap);
-  launch_k(c, k_coarse_pack_long, c->sm_count * 2, kBlock, st, s.large, s.ctr + kCtrLarge, s.ub_ptr, s.c_cnt, c_rowptr,
-                                                         s.tmp, c_colind, s.ctr + kCtrErr, s.ctr + kCtrCnnz,
-                                                         c_colind_cap);
-  c->launches += 2;
+  launch_k(c, k_pack_chunks, 1, kBlock, st, s.large, s.ctr + kCtrLarge, s.c_cnt, s.chunk_off, s.ctr + kCtrErr,
+           s.ctr + kCtrCnnz, c_colind_cap);
+  launch_k(c, k_coarse_pack_long, c->sm_count * 4, kBlock, st, s.large, s.ctr + kCtrLarge, s.chunk_off, s.ub_ptr,
+           s.c_cnt, c_rowptr, s.tmp, c_colind, s.ctr + kCtrErr, s.ctr + kCtrCnnz, c_colind_cap);
+  c->launches += 3;
   timer_end(c, st);
   MIS2_CUDA(cudaGetLastError());
   return MIS2_OK;
