@@ -6,7 +6,7 @@ MIS-2 (Algorithm 1), aggregation (Algorithm 3) and the coarse graph.  The
 metric is edges/s = input entries per step / step time.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 27pt|small|rmat|serve|ablation|setup]
+                  [--workload 27pt|small|rmat|serve|ablation|setup|timeline]
 
 - value: device-resident input, CUDA events around each step, L2 flushed
   (256 MiB write) before every step, outside the timed interval.
@@ -885,6 +885,47 @@ def _traffic_from_profile(kernel):
         return None
 
 
+def run_timeline(args):
+    """--workload timeline: GPU activity trace (CUPTI) of one coarsening level
+    of --graph (27pt, small or rmat), with the short kernels launched with
+    programmatic dependent launch (the default) and serially; per case the
+    level's span, the time covered by at least one operation, the idle time
+    between operations and every operation in order.  Not a bench value (the
+    trace itself costs a little per operation)."""
+    import torch
+
+    from paper_2204_02934_gb300 import mis2, trace
+
+    g, desc = _workload(args.graph)
+    dev = torch.device("cuda", 0)
+    dg = mis2.DeviceGraph.from_host(g, dev)
+    n = g.n
+    bufs = [torch.empty(n, dtype=torch.uint8, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+            torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n + 1, dtype=torch.int32, device=dev),
+            torch.empty(g.nnz, dtype=torch.int32, device=dev)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    cases = {}
+    for label, serial in (("overlapped", 0), ("serial", 1)):
+        ctx = mis2.Context(g.n, g.nnz, loop=mis2.MIS2_LOOP_DEVICE, serial_launches=serial)
+        step = lambda: mis2.mis2_coarsen_level(ctx.handle, dg.csr, 0, *bufs, g.nnz, stream)
+        for _ in range(max(args.warmup, 3)):
+            flush.fill_(1)
+            step()
+        flush.fill_(1)
+        with trace.GpuTrace() as t:
+            step()
+        ctx.close()
+        t0 = t.records[0]["start_ns"] if t.records else 0
+        cases[label] = dict(trace.summary(t.records), timeline=[
+            [round((r["start_ns"] - t0) / 1e3, 1), round((r["end_ns"] - r["start_ns"]) / 1e3, 1),
+             trace.short_name(r["name"]) if r["kind"] == "kernel" else r["name"]] for r in t.records])
+    print(json.dumps({"workload": desc, "timeline": cases,
+                      "note": "one level after 3 warm-up levels, L2 flushed before it; start and duration in us"}),
+          flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -892,7 +933,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="27pt", choices=["27pt", "small", "rmat", "serve", "ablation",
-                                                                    "setup"])
+                                                                    "setup", "timeline"])
+    ap.add_argument("--graph", default="27pt", choices=["27pt", "small", "rmat"], help="timeline: the level's graph")
     ap.add_argument("--loop", default="device", choices=["device", "host"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
@@ -912,6 +954,8 @@ def main():
         return run_ablation(args)
     if args.workload == "setup":
         return run_setup(args)
+    if args.workload == "timeline":
+        return run_timeline(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
