@@ -354,7 +354,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": "k_mis_loop (MIS-2 rounds, device loop)",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_kind": peak_kind, "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS,
-                    "traffic": _traffic_from_profile("k_mis_loop"),
+                    "traffic": _traffic_from_profile("k_mis_loop", args.workload),
                     "bytes_per_step": loop_bytes / args.steps,
                     "kernel_ms_per_step": dom_ms / args.steps,
                     "launches_per_step": int(kernel_launch[dom] // args.steps)}
@@ -863,9 +863,10 @@ def run_setup(args):
     return 0
 
 
-def _traffic_from_profile(kernel):
-    """dram bytes per launch recorded by an ncu capture of this kernel, when
-    the recorded source digest still matches the library sources."""
+def _traffic_from_profile(kernel, workload):
+    """dram bytes per launch recorded by an ncu capture of this kernel on this
+    workload, when the recorded source digest still matches the library
+    sources (None otherwise)."""
     p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -878,7 +879,7 @@ def _traffic_from_profile(kernel):
         from paper_2204_02934_gb300 import _build
 
         files = vals["source_files"].split() if "source_files" in vals else None
-        if vals.get("source_digest") != _build.source_digest(files):
+        if vals.get("workload_key") != workload or vals.get("source_digest") != _build.source_digest(files):
             return None
         return float(vals["dram_bytes_per_launch"])
     except Exception:

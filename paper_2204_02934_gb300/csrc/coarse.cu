@@ -236,11 +236,14 @@ __device__ __forceinline__ void warp_sort_keys(uint32_t (&k)[K]) {
   }
 }
 
+// rest / rest_cnt: the aggregates with fine entries that are not small are
+// listed there (one reservation per warp and window), so that the kernel
+// for the others visits those alone.
 template <typename I>
 __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const int32_t* labels, int64_t n_aggs,
                                                          const int32_t* agg_ptr, const int32_t* members,
                                                          const int32_t* ub, const int32_t* ub_ptr, int32_t* tmp,
-                                                         int32_t* c_cnt) {
+                                                         int32_t* c_cnt, int32_t* rest, int32_t* rest_cnt) {
   pdl_enter();
   __shared__ int32_t sh_cnt[kBlock / 32][32];
   __shared__ int32_t sh_sel[kBlock / 32][32];
@@ -258,6 +261,7 @@ __global__ void __launch_bounds__(kBlock) k_coarse_small(GraphView<I> g, const i
     // an aggregate without fine entries (an isolated vertex) has an empty row
     if (in && u == 0) c_cnt[a] = 0;
     const bool sm = in && u > 0 && small_aggregate(p1 - p0, u, true);
+    warp_append(in && u > 0 && !sm, (int32_t)a, rest, rest_cnt);
     const int32_t outb = sm ? ub_ptr[a] : 0;
     const int m = sm ? p1 - p0 : 0;
     const int um = sm ? u : 0;
@@ -1028,10 +1032,9 @@ static int coarse_rows_launch(mis2_ctx* c, const GraphView<I>& gv, const int32_t
                               bool small_on, cudaStream_t st, bool cand_ready = false, bool ctr_fresh = false) {
   Scratch& s = c->s;
   const int rows_blocks = grid_for(c, n_aggs, kCoarseWarps, 16);
-  if (small_on) {
+  if (small_on) {  // the aggregates k_coarse_small listed in s.left_mid
     launch_k(c, k_coarse_rows<I>, rows_blocks, kCoarseWarps * 32, st, gv, labels, n_aggs, s.agg_ptr, s.members, s.ub,
-                                                                s.ub_ptr, s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge,
-                                                                small_on, nullptr, nullptr);
+             s.ub_ptr, s.tmp, s.c_cnt, s.large, s.ctr + kCtrLarge, small_on, s.left_mid, s.ctr + kCtrCoarseRest);
     c->launches++;
     return MIS2_OK;
   }
@@ -1153,8 +1156,10 @@ static int coarsen_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels, int
   // entries per aggregate at most half the sub-batch
   const bool small_on = n_aggs < ((int64_t)1 << kSmallLabelBits) && g.nnz <= (int64_t)(kSmallEntries / 2) * n_aggs;
   if (small_on) {
-    launch_k(c, k_coarse_small<I>, grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, st, 
-        gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
+    MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
+    launch_k(c, k_coarse_small<I>, grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock,
+             st, gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt, s.left_mid,
+             s.ctr + kCtrCoarseRest);
     c->launches++;
   }
   MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st));
@@ -1252,8 +1257,10 @@ static int coarsen_fast_t(mis2_ctx* c, const GraphArgs& g, const int32_t* labels
   // entries per aggregate at most half the sub-batch
   const bool small_on = n_aggs < ((int64_t)1 << kSmallLabelBits) && g.nnz <= (int64_t)(kSmallEntries / 2) * n_aggs;
   if (small_on) {
-    launch_k(c, k_coarse_small<I>, grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock, st, 
-        gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt);
+    if (!ctr_fresh) MIS2_CUDA(cudaMemsetAsync(s.ctr + kCtrCoarseRest, 0, sizeof(int32_t), st));
+    launch_k(c, k_coarse_small<I>, grid_for(c, (n_aggs + kSmallWindow - 1) / kSmallWindow, kBlock / 32, 8), kBlock,
+             st, gv, labels, n_aggs, s.agg_ptr, s.members, s.ub, s.ub_ptr, s.tmp, s.c_cnt, s.left_mid,
+             s.ctr + kCtrCoarseRest);
     c->launches++;
   }
   MIS2_TRY(coarse_rows_launch<I>(c, gv, labels, n_aggs, small_on, st, cand_ready, ctr_fresh));

@@ -34,11 +34,12 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
     prof = tmp_path / "profiles"
     prof.mkdir()
     rec = prof / "k_test_traffic.txt"
-    rec.write_text(f"kernel: k_test\ndram_bytes_per_launch: 1234\nsource_files: {' '.join(files)}\n"
-                   f"source_digest: {_build.source_digest(files)}\n")
+    rec.write_text(f"kernel: k_test\nworkload_key: 27pt\ndram_bytes_per_launch: 1234\n"
+                   f"source_files: {' '.join(files)}\nsource_digest: {_build.source_digest(files)}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic_from_profile("k_test") == 1234.0
-    rec.write_text(f"kernel: k_test\ndram_bytes_per_launch: 1234\nsource_files: {' '.join(files)}\n"
-                   "source_digest: 0000000000000000\n")
-    assert bench._traffic_from_profile("k_test") is None  # the kernel changed since the capture
-    assert bench._traffic_from_profile("k_missing") is None
+    assert bench._traffic_from_profile("k_test", "27pt") == 1234.0
+    assert bench._traffic_from_profile("k_test", "rmat") is None  # taken on another workload
+    rec.write_text(f"kernel: k_test\nworkload_key: 27pt\ndram_bytes_per_launch: 1234\n"
+                   f"source_files: {' '.join(files)}\nsource_digest: 0000000000000000\n")
+    assert bench._traffic_from_profile("k_test", "27pt") is None  # the kernel changed since the capture
+    assert bench._traffic_from_profile("k_missing", "27pt") is None
