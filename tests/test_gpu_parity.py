@@ -399,3 +399,52 @@ def test_timing_loop_mode_brackets_the_loop_alone():
     with pytest.raises(mis2.Mis2Error):
         ctx.configure(timing=3)
     ctx.close()
+
+
+def _hub_leftover_graph():
+    """A 160x160 grid plus hubs of 40, 600 and 9,000 neighbours, and roots
+    chosen (greedily, more than two hops apart in the whole graph) among the
+    grid vertices no hub touches: the hubs are phase-3 leftovers of every row
+    class (a warp with a hash table, a block sort, the block windows above
+    8,192 entries)."""
+    side = 160
+    base = gg.grid2d_5pt(side, side)
+    pairs = [gg_pairs(base)]
+    degs = (40, 600, 9000)
+    for h, d in enumerate(degs):
+        nb = (np.arange(d, dtype=np.int64) * (base.n // d) + 17 * h) % base.n
+        pairs.append(np.stack([np.full(d, base.n + h, dtype=np.int64), nb], axis=1))
+    g = gg.graph_from_edges(base.n + len(degs), np.concatenate(pairs))
+    rp, ci = g.rowptr.astype(np.int64), g.colind
+    touched = np.zeros(g.n, dtype=bool)
+    touched[base.n:] = True
+    touched[ci[rp[base.n]:]] = True
+    blocked = np.zeros(g.n, dtype=bool)
+    roots = []
+    for v in range(base.n):
+        if touched[v] or blocked[v]:
+            continue
+        roots.append(v)
+        ring = ci[rp[v]:rp[v + 1]]
+        two = np.concatenate([ci[rp[w]:rp[w + 1]] for w in ring] + [ring, [v]])
+        blocked[two] = True  # anything within two hops of a root is not a root
+        for w in ring:  # ... and within two hops of those: keeps roots > 2 apart
+            blocked[ci[rp[w]:rp[w + 1]]] = True
+    return g, np.array(roots, dtype=np.int32)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_phase3_rows_of_every_class_match_the_oracle(mode):
+    import torch
+
+    g, roots = _hub_leftover_graph()
+    in_set = np.zeros(g.n, dtype=np.uint8)
+    in_set[roots] = 1
+    ref_labels, ref_na = oracle.aggregate(g, in_set, seed=3, mode=mode)[:2]
+    assert (ref_labels[-3:] >= 0).all()
+    ctx = make_ctx(g, loop=mis2.MIS2_LOOP_DEVICE, debug_checks=mis2.MIS2_DEBUG_VALIDATE)
+    dg = mis2.DeviceGraph.from_host(g)
+    labels, na = ctx.aggregate(dg, torch.from_numpy(roots).to(dg.rowptr.device), seed=3, mode=mode)
+    assert na == ref_na
+    assert np.array_equal(labels.cpu().numpy(), ref_labels)
+    ctx.close()
