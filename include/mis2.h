@@ -416,9 +416,11 @@ typedef struct {
   int64_t mem_budget;     /* bytes of request buffers admitted at once (default 8 GiB) */
   int64_t slot_max_n;     /* largest request (batch_max >= 2: largest union) per slot (vertices, entries) */
   int64_t slot_max_nnz;
-  mis2_config cfg;        /* per-slot configuration (default loop: MIS2_LOOP_DEVICE; the slots
-                             share a lock so that one device-loop kernel runs at a time, the
-                             other steps of their requests overlap freely) */
+  mis2_config cfg;        /* per-slot configuration.  Default loop: MIS2_LOOP_HOST, whose
+                             per-round kernels of different requests interleave on the GPU;
+                             with MIS2_LOOP_DEVICE the slots share a lock so that one
+                             device-loop kernel runs at a time (the other steps of their
+                             requests overlap freely), which suits a single slot best */
 } mis2_server_config;
 
 typedef struct {

@@ -369,7 +369,9 @@ void mis2_server_config_default(mis2_server_config* c) {
   c->slot_max_n = (int64_t)1 << 22;
   c->slot_max_nnz = (int64_t)1 << 25;
   mis2_config_default(&c->cfg);
-  c->cfg.loop = MIS2_LOOP_DEVICE;
+  // several slots: the host-driven rounds of different requests interleave
+  // on the GPU, where device-loop kernels would run one at a time
+  c->cfg.loop = MIS2_LOOP_HOST;
 }
 
 int mis2_server_create(mis2_server** out, const mis2_server_config* cfg) {
