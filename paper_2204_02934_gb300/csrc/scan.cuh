@@ -4,7 +4,11 @@
 // of the tiles before it itself (two launches); above that a one-block scan
 // of the tile counts runs in between (three).  Used for the root list
 // (ascending vertex ids), the phase-2 root ranking and the CSR row pointers
-// of the coarse graph.
+// of the coarse graph.  Within a tile, item k of thread t is item
+// k * kBlock + t, so that every load and store of the items is coalesced
+// across the warp; the order of a tile's items is (k, warp, lane), and the
+// rewrite ranks them in that order (a ballot or a warp scan per k, then the
+// 64 (k, warp) totals scanned by one warp).
 #pragma once
 
 #include "common.cuh"
@@ -15,6 +19,8 @@ constexpr int kScanIpt = 8;                    // items per thread
 constexpr int kScanTile = kBlock * kScanIpt;   // items per tile
 
 constexpr int64_t kScanDirectTiles = 4096;   // 8.4 M items
+constexpr int kScanWarps = kBlock / 32;
+static_assert(kScanIpt * kScanWarps == 64, "one warp scans a tile's (k, warp) totals two to a lane");
 
 inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
@@ -28,6 +34,33 @@ __device__ __forceinline__ int tile_offset(const int32_t* tile_cnt, int64_t tile
   return block_sum_i32(x, sh);
 }
 
+// In place: wcnt[k * kScanWarps + w] (the count of item k over warp w of one
+// tile) becomes the exclusive prefix over the tile's (k, w) order; returns
+// the tile total.  Every thread of the block calls it; starts with a barrier
+// (the counts' writes are then visible) and ends with one.
+__device__ __forceinline__ int tile_warp_offsets(int* wcnt, int* total_sh) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const int a = wcnt[lane], b = wcnt[32 + lane];
+    int ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int ya = __shfl_up_sync(kFull, ia, o), yb = __shfl_up_sync(kFull, ib, o);
+      if (lane >= o) {
+        ia += ya;
+        ib += yb;
+      }
+    }
+    const int ta = __shfl_sync(kFull, ia, 31);
+    wcnt[lane] = ia - a;
+    wcnt[32 + lane] = ta + ib - b;
+    if (lane == 31) *total_sh = ta + ib;
+  }
+  __syncthreads();
+  return *total_sh;
+}
+
 // Pred: struct with `__device__ bool operator()(int64_t i) const`.
 template <class Pred>
 __global__ void __launch_bounds__(kBlock) k_tile_count(int64_t n, Pred pred, int32_t* tile_cnt) {
@@ -35,10 +68,10 @@ __global__ void __launch_bounds__(kBlock) k_tile_count(int64_t n, Pred pred, int
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
     int c = 0;
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanIpt;
+    const int64_t base = tile * kScanTile + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
-      const int64_t i = base + k;
+      const int64_t i = base + (int64_t)k * kBlock;
       if (i < n && pred(i)) c++;
     }
     c = block_sum_i32(c, sh);
@@ -53,10 +86,10 @@ __global__ void __launch_bounds__(kBlock) k_tile_sum(int64_t n, Val val, int32_t
   __shared__ int sh[40];
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
     int c = 0;
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanIpt;
+    const int64_t base = tile * kScanTile + threadIdx.x;
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
-      const int64_t i = base + k;
+      const int64_t i = base + (int64_t)k * kBlock;
       if (i < n) c += val(i);
     }
     c = block_sum_i32(c, sh);
@@ -77,28 +110,31 @@ __global__ void __launch_bounds__(kBlock) k_tile_compact(int64_t n, Pred pred, c
                                                           Emit emit, bool direct, int32_t* total_out) {
   pdl_enter();
   __shared__ int sh[40];
+  __shared__ int wcnt[kScanIpt * kScanWarps];
+  __shared__ int total_sh;
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const unsigned below = (1u << lane) - 1u;
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanIpt;
+    const int64_t base = tile * kScanTile + threadIdx.x;
     bool keep[kScanIpt];
-    int c = 0;
+    int rank[kScanIpt];
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
-      const int64_t i = base + k;
+      const int64_t i = base + (int64_t)k * kBlock;
       keep[k] = i < n && pred(i);
-      c += keep[k];
+      const unsigned b = __ballot_sync(kFull, keep[k]);
+      rank[k] = __popc(b & below);
+      if (lane == 0) wcnt[k * kScanWarps + w] = __popc(b);
     }
     const int off = tile_offset(tile_off, tile, direct, sh);
-    int total;
-    int pos = block_exclusive_scan(c, sh, &total) + off;
+    const int total = tile_warp_offsets(wcnt, &total_sh);
     if (direct && total_out != nullptr && threadIdx.x == 0 && (tile + 1) * kScanTile >= n) *total_out = off + total;
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
-      const int64_t i = base + k;
-      if (i < n) {
-        emit(i, pos, keep[k]);
-        pos += keep[k];
-      }
+      const int64_t i = base + (int64_t)k * kBlock;
+      if (i < n) emit(i, off + wcnt[k * kScanWarps + w] + rank[k], keep[k]);
     }
+    __syncthreads();  // wcnt and total_sh are rewritten for the next tile
   }
 }
 
@@ -110,30 +146,40 @@ __global__ void __launch_bounds__(kBlock) k_tile_scan_write(int64_t n, Val val, 
                                                              O* out, O* out2, bool direct, int32_t* total_out) {
   pdl_enter();
   __shared__ int sh[40];
+  __shared__ int wcnt[kScanIpt * kScanWarps];
+  __shared__ int total_sh;
+  const int lane = lane_id(), w = threadIdx.x >> 5;
   for (int64_t tile = blockIdx.x; tile * kScanTile < n; tile += gridDim.x) {
-    const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanIpt;
-    int v[kScanIpt];
-    int c = 0;
+    const int64_t base = tile * kScanTile + threadIdx.x;
+    int ex[kScanIpt];  // exclusive prefix of item k within its warp
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
-      const int64_t i = base + k;
-      v[k] = i < n ? val(i) : 0;
-      c += v[k];
+      const int64_t i = base + (int64_t)k * kBlock;
+      const int v = i < n ? val(i) : 0;
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      ex[k] = incl - v;
+      if (lane == 31) wcnt[k * kScanWarps + w] = incl;
     }
     const int off = tile_offset(tile_off, tile, direct, sh);
-    int total;
-    int pos = block_exclusive_scan(c, sh, &total) + off;
-    if (direct && total_out != nullptr && threadIdx.x == 0 && (tile + 1) * kScanTile >= n) *total_out = off + total;
+    const int total = tile_warp_offsets(wcnt, &total_sh);
+    const bool last = (tile + 1) * kScanTile >= n;
+    if (direct && total_out != nullptr && threadIdx.x == 0 && last) *total_out = off + total;
 #pragma unroll
     for (int k = 0; k < kScanIpt; k++) {
-      const int64_t i = base + k;
+      const int64_t i = base + (int64_t)k * kBlock;
       if (i < n) {
+        const int pos = off + wcnt[k * kScanWarps + w] + ex[k];
         out[i] = (O)pos;
         if (out2 != nullptr) out2[i] = (O)pos;
       }
-      pos += v[k];
     }
-    if (base <= n - 1 && n - 1 < base + kScanIpt) out[n] = (O)pos;  // thread holding the last item
+    if (last && threadIdx.x == 0) out[n] = (O)(off + total);
+    __syncthreads();  // wcnt and total_sh are rewritten for the next tile
   }
 }
 
